@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark: MINRES solves/s at true relative residual 1e-8 for the
+complex-shifted Laplacian solve (K + lambda I) z = f with the absolute-value
+preconditioner (arXiv 2408.00488), on the 2D n=1023 workload:
+a(x, y) = exp(ln(10) x y), lambda = 100i, f ~ U[-1,1] + i U[-1,1] (seed 1).
+
+A step is one whole solve (ingest, P^{-1} b, the MINRES loop with its
+stopping test, egress) with f already resident in HBM.  The headline `value`
+is the FP32-preconditioner form (sine transforms and scale of P^{-1} in FP32;
+stencil, Lanczos, Givens and residual norms in FP64); the plain FP64 form is
+timed beside it under "forms".  Both must reach relres <= 1e-8.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl csl|reference]
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the solve
+("replicas only": the method has no exchange step), value = total solves/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MINRES solves/s at relres 1e-8 (2D n=1023, a=exp(ln10*x*y), lambda=100i)"
+UNIT = "solves/s"
+WORKLOAD = ("config1: 2D unit square, n=1023 (M=1,046,529), 5-point FD of -div(a grad), "
+            "a=exp(ln10*x*y) at face midpoints, lambda=0+100i, f~U[-1,1]^2 seed 1, tol 1e-8")
+TOL = 1e-8
+MAXIT = 2000
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 / FP32 ALU peaks derived from unit counts and the maximum SM clock:
+# 152 SMs x 2 FP64 FMA/clk (x 2 flops) x 2.07 GHz, and 152 x 128 FP32 FMA/clk.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def golden_iters(name):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.txt")
+    try:
+        with open(p) as fh:
+            for line in fh:
+                if line.startswith(name + " "):
+                    return int(line.split()[1])
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def kernel_model(name, M, d, prec, N):
+    """Algorithmic bytes and flops per launch of one kernel of a MINRES
+    iteration (M grid points, d dims, line length N = n+1 of the pass axis)."""
+    sT = 16 if prec == "fp64" else 8
+    dst_flops = 11 + 5 * math.log2(N)  # per complex point per sine transform (pre, FFT, split, scan)
+    f64 = f32 = 0.0
+    if name == "k_stencil":
+        b = sT + 16 + 16 + 8 + 8 * d
+        f64 = 16 + 8 * d
+    elif name.startswith("k_row<LOAD_LANCZOS"):
+        b = 16 + 16 + 16 + sT
+        f64 = 4
+        if prec == "fp64":
+            f64 += dst_flops
+        else:
+            f32 += dst_flops
+    elif name.startswith("k_row<LOAD_T,STORE_Z_UPDATE"):
+        b = sT + sT + 48 + sT + 32
+        f64 = 14
+        if prec == "fp64":
+            f64 += dst_flops
+        else:
+            f32 += dst_flops
+    elif name == "k_strided<mid>":
+        b = 2 * sT + (8 if prec == "fp64" else 0)
+        fl = 2 * dst_flops + 7
+        if prec == "fp64":
+            f64 += fl
+        else:
+            f32 += fl
+    else:  # plain strided transform (3D y passes)
+        b = 2 * sT
+        if prec == "fp64":
+            f64 += dst_flops
+        else:
+            f32 += dst_flops
+    return b * M, f64 * M, f32 * M
+
+
+def roofline_table(kernels, M, d, prec, n, hbm_gbs, iters):
+    out = []
+    per_iter_ms = sum(ms for _, ms in kernels)
+    for name, ms in kernels:
+        N = n + 1
+        B, F64, F32 = kernel_model(name, M, d, prec, N)
+        s = ms / 1e3
+        t_hbm = B / (hbm_gbs * 1e9)
+        t64 = F64 / (FP64_PEAK_TFLOPS * 1e12)
+        t32 = F32 / (FP32_PEAK_TFLOPS * 1e12)
+        if t64 >= max(t_hbm, t32):
+            bound, achieved, peak, unit = "alu", F64 / s / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+        elif t32 > t_hbm:
+            bound, achieved, peak, unit = "alu", F32 / s / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
+        else:
+            bound, achieved, peak, unit = "hbm", B / s / 1e9, hbm_gbs, "GB/s"
+        out.append({"kernel": name, "ms": round(ms, 5), "share": round(ms / per_iter_ms, 4),
+                    "alg_bytes": int(B), "fp64_flops": int(F64), "fp32_flops": int(F32),
+                    "hbm_gbs": round(B / s / 1e9, 1), "hbm_frac": round(B / s / 1e9 / hbm_gbs, 4),
+                    "fp64_tflops": round(F64 / s / 1e12, 4),
+                    "bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": unit,
+                    "frac": round(achieved / peak, 4)})
+    return out
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(budget_s=12.0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: k MINRES
+    iterations of the same solve; returns (seconds per iteration, k)."""
+    import numpy as np
+    import oracle
+    import workloads as W
+
+    s = W.config1()
+    t = time.perf_counter()
+    oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=1)
+    t1 = time.perf_counter() - t
+    k = max(2, min(40, int(budget_s / max(t1, 1e-3))))
+    t = time.perf_counter()
+    _, info = oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=k)
+    dt = time.perf_counter() - t
+    return dt / info.iters, info.iters
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import workloads as W
+
+    iters_full = golden_iters("config1")
+    s = W.config1()
+    k_per_step = 3
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, info = oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=k_per_step)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt / info.iters)
+    per_iter = statistics.mean(times)
+    value = 1.0 / (per_iter * iters_full) if iters_full else None
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * k_per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step = {k_per_step} MINRES iterations of the workload's solve "
+                                       f"(oracle.solve, FP64 NumPy, dense O(n^2) DST-I); solves/s = "
+                                       f"1 / (s per iteration x {iters_full} iterations of the full oracle solve)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="csl", choices=["csl", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2408_00488_gb300 as csl
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    s = W.config1()
+    n, d, M = s.n, s.dim, s.M
+    faces = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in s.faces]
+    f = torch.from_numpy(np.ascontiguousarray(s.f)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MiB)
+    hbm_gbs, hbm_src = read_peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, K):
+        """K steps, each bracketed by CUDA events on the current stream, L2
+        flushed (outside the events) before every step; returns mean ms."""
+        ms = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(K):
+            flush.zero_()
+            e0.record()
+            info = fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms), info
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    forms = {}
+    plans = {}
+    for prec in ("fp32", "fp64"):
+        plans[prec] = csl.Plan(faces, s.lam, precision=prec)
+        z = torch.empty_like(f)
+        for _ in range(args.warmup):
+            _, info = plans[prec].solve(f, tol=TOL, maxit=MAXIT, out=z)
+        assert info.converged and info.relres <= TOL, (prec, info)
+
+    gpu_id = "0"
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    sampler = ClockSampler(gpu_id)
+
+    # ---- timed region: headline form (FP32 preconditioner) -------------------
+    z = torch.empty_like(f)
+    barrier()
+    sampler.start()
+    ms_mixed, info_mixed = timed(lambda: plans["fp32"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps)
+    barrier()
+    clocks = sampler.stop()
+    ms_mixed = max_over_ranks(ms_mixed)
+    assert info_mixed.converged and info_mixed.relres <= TOL
+    forms["fp32_precond"] = {"solves_per_s": world * 1e3 / ms_mixed, "ms_per_solve": ms_mixed,
+                             "iters": info_mixed.iters, "relres": info_mixed.relres,
+                             "launches_per_solve": info_mixed.launches}
+
+    # ---- plain FP64 form ---------------------------------------------------
+    barrier()
+    ms_64, info_64 = timed(lambda: plans["fp64"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps)
+    barrier()
+    ms_64 = max_over_ranks(ms_64)
+    assert info_64.converged and info_64.relres <= TOL
+    forms["fp64"] = {"solves_per_s": world * 1e3 / ms_64, "ms_per_solve": ms_64, "iters": info_64.iters,
+                     "relres": info_64.relres, "launches_per_solve": info_64.launches}
+
+    # ---- end to end through the C ABI with host buffers (pinned) -------------
+    fh = torch.from_numpy(np.ascontiguousarray(s.f)).pin_memory()
+    zh = torch.empty_like(fh).pin_memory()
+    for _ in range(2):
+        plans["fp32"].solve_host(fh, zh, tol=TOL, maxit=MAXIT)
+    barrier()
+    ms_e2e, info_e2e = timed(lambda: plans["fp32"].solve_host(fh, zh, tol=TOL, maxit=MAXIT), args.steps)
+    barrier()
+    ms_e2e = max_over_ranks(ms_e2e)
+    assert info_e2e.converged
+
+    # ---- per-kernel durations (CUDA events on the launching stream) --------
+    kern = {}
+    for prec, key in (("fp32", "fp32_precond"), ("fp64", "fp64")):
+        p = plans[prec]
+        p.solve(f, tol=TOL, maxit=MAXIT, out=z)  # real data in the vectors
+        kt = p.time_kernels(args.kernel_reps)
+        kern[key] = roofline_table(kt, M, d, prec, n, hbm_gbs, forms[key]["iters"])
+    head = kern["fp32_precond"]
+    dom = max(head, key=lambda r: r["ms"])
+    roofline = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"],
+                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "peak_source": (f"HBM {hbm_src} (MEASURED_PEAKS.json)" if dom["bound"] == "hbm" else
+                                "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.196 TFLOP/s)")}
+    # whole-solve HBM fraction of the headline form: algorithmic bytes per iteration
+    bytes_iter = sum(r["alg_bytes"] for r in head)
+    solve_bytes = bytes_iter * info_mixed.iters
+    hbm_pct_solve = solve_bytes / (ms_mixed / 1e3) / (hbm_gbs * 1e9)
+
+    # ---- CPU baseline: the oracle on a bounded sample ----------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_iter, k = cpu_oracle_sample()
+        it_full = golden_iters("config1") or info_64.iters
+        cpu = {"value": 1.0 / (per_iter * it_full), "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+               "kind": "oracle",
+               "sample": f"{k} MINRES iterations of this workload's solve by oracle.solve (FP64 NumPy, "
+                         f"dense O(n^2) DST-I, explicit residual per iteration); solves/s = 1/(s per iteration "
+                         f"x {it_full} iterations of the full oracle solve)"}
+
+    if rank == 0:
+        bytes_io = 16 * M
+        line = {
+            "metric": METRIC, "value": world * 1e3 / ms_mixed, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 inside P^-1)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "FP32-preconditioner MINRES (FP64 stencil/Lanczos/Givens)",
+                       "l2": "flushed (256 MiB write) before every step", "parallelism": "replicas" if world > 1
+                       else "single GPU"},
+            "forms": forms,
+            "roofline": roofline,
+            "solve_hbm_frac": round(hbm_pct_solve, 4),
+            "kernels": kern,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": info_mixed.launches * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * csl.h -- C ABI of the GB300 solver for complex-shifted Laplacian systems
+ *
+ *     (K + lambda I) z = f,   lambda = alpha + i beta            (Eq. 1)
+ *
+ * where K is the conservative finite-difference discretisation of
+ * -div(a grad .) on the unit square (5-point) or cube (7-point) with
+ * homogeneous Dirichlet boundary values and n_d interior points per axis
+ * (h_d = 1/(n_d+1)).  The solve is preconditioned MINRES on the equivalent
+ * 2x2 block real system (Eq. 2)
+ *
+ *     A = [[beta I, K + alpha I], [K + alpha I, -beta I]],  A [z1; z2] = [Im f; Re f],
+ *
+ * with z = z1 + i z2, and the absolute-value preconditioner of Eq. 4
+ *
+ *     P = blkdiag(sqrt((gamma L + alpha I)^2 + beta^2 I), same),  gamma = sqrt(a_min a_max),
+ *
+ * applied through the sine transform that diagonalises the constant-coefficient
+ * Laplacian L (Section 2.3).  When a is constant, P is |A| (Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Grids: dim = 2 or 3; n[0], n[1], n[2] are the interior point counts along
+ *    x, y, z (n[2] ignored for dim = 2).  Every n[d] + 1 must be a power of two
+ *    between 4 and 2048 (else CSL_UNSUPPORTED_SIZE).
+ *  - Grid vectors are C-order arrays with x fastest: point (ix, iy[, iz]) at
+ *    index ix + n[0]*(iy + n[1]*iz).  "complex128" vectors hold interleaved
+ *    (re, im) doubles; "block-pair" vectors hold (block-1, block-2) doubles of
+ *    the block system interleaved the same way.
+ *  - Coefficient samples: coef_faces[0] are the x-faces, shape
+ *    ([n2,] n1, n0+1), entry i along x being the face between grid indices
+ *    i-1 and i (at x = (i + 1/2) h_x); coef_faces[1] the y-faces
+ *    ([n2,] n1+1, n0); coef_faces[2] the z-faces (n2+1, n1, n0).  All > 0.
+ *  - Pointers are DEVICE pointers owned by the caller unless the name ends in
+ *    _host.  A plan owns its own workspace and copies the coefficients; the
+ *    caller may free them after csl_plan_create returns.
+ *  - All work runs on the plan's CUDA stream (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  Calls that return a csl_solve_info
+ *    synchronise that stream; the others are stream-ordered and asynchronous.
+ *  - Nothing throws across the ABI: every call returns a csl_status.
+ */
+#ifndef CSL_H
+#define CSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum csl_status {
+  CSL_OK = 0,
+  CSL_INVALID_ARG = 1,       /* null pointer, dim not 2/3, n < 1, non-finite shift, coefficient <= 0 */
+  CSL_UNSUPPORTED_SIZE = 2,  /* n[d] + 1 not a power of two in [4, 2048] */
+  CSL_SINGULAR_PRECOND = 3,  /* some (gamma mu_k + alpha)^2 + beta^2 == 0 (only possible when beta == 0) */
+  CSL_BREAKDOWN = 4,         /* non-finite or negative <P^{-1} v, v> in the Lanczos process */
+  CSL_NOT_CONVERGED = 5,     /* maxit reached; z holds the last iterate, info is filled */
+  CSL_TIMEOUT = 6,           /* a bounded device wait expired */
+  CSL_CUDA_ERROR = 7,        /* a CUDA runtime call failed */
+  CSL_OUT_OF_MEMORY = 8
+} csl_status;
+
+typedef enum csl_precision {
+  CSL_PREC_FP64 = 0,  /* every step in FP64 (the plain method)                          */
+  CSL_PREC_FP32 = 1   /* sine transforms and per-mode scale of P^{-1} in FP32; stencil,
+                         Lanczos recurrence, Givens rotations and residual norms in FP64 */
+} csl_precision;
+
+typedef struct csl_plan_options {
+  int precision;          /* csl_precision, default CSL_PREC_FP64                          */
+  double gamma_override;  /* > 0: use this gamma in P; otherwise sqrt(min a * max a) (Eq. 4) */
+  int lines_per_cta;      /* sine-transform lines per CTA for the strided passes; 0 = tuned */
+  int use_graph;          /* 1 (default): the iteration loop runs as a CUDA graph with a
+                             device-controlled WHILE node; 0: host-driven loop              */
+  int reserved[8];
+} csl_plan_options;
+
+typedef struct csl_solve_info {
+  int iters;          /* MINRES iterations = products with A in the loop ("Iter", Section 3) */
+  int status;         /* csl_status of the solve                                             */
+  double relres;      /* true ||f - (K + lambda I) z||_2 / ||f||_2 of the returned z          */
+  double pnorm;       /* |eta|: the P^{-1}-norm residual estimate of MINRES at exit           */
+  double gamma;       /* gamma used by P                                                      */
+  int checks;         /* explicit true-residual evaluations performed                         */
+  int launches;       /* kernels this library launched for the solve                           */
+  int reserved[6];
+} csl_solve_info;
+
+typedef struct csl_plan csl_plan;
+
+/* Library version string and status names (static storage, never NULL). */
+const char* csl_version(void);
+const char* csl_status_string(csl_status s);
+
+/* Description of the last CUDA failure seen by this thread ("" if none). */
+const char* csl_last_error(void);
+
+/* Fill *opt with the defaults above. */
+csl_status csl_plan_options_init(csl_plan_options* opt);
+
+/*
+ * Build a plan for one grid, one coefficient field and one shift
+ * (Eq. 1, Eq. 4, Section 2.3): scales and copies the face samples, forms the
+ * stencil diagonal, gamma = sqrt(a_min a_max), the per-axis Laplacian
+ * eigenvalues mu_k = (4/h^2) sin^2(k pi / (2(n+1))), the per-mode scale of
+ * P^{-1}, the FFT twiddles, and allocates the MINRES workspace
+ * (about 10 vectors of 16 bytes per grid point).
+ * coef_faces: `dim` device pointers (layout above).  opt may be NULL.
+ * On success *out owns device memory until csl_plan_destroy.
+ */
+csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3],
+                           const double* const coef_faces[3], double alpha, double beta,
+                           const csl_plan_options* opt, void* stream);
+void csl_plan_destroy(csl_plan* plan);
+
+/* Change the stream later calls run on. */
+csl_status csl_plan_set_stream(csl_plan* plan, void* stream);
+
+/* Device bytes owned by the plan. */
+size_t csl_plan_workspace_bytes(const csl_plan* plan);
+
+/* gamma actually used by P (Eq. 4). */
+double csl_plan_gamma(const csl_plan* plan);
+
+/*
+ * out = (K + lambda I) z for complex128 z, out (M entries each); Eq. 1's
+ * operator, evaluated by the same stencil kernel the solver uses.  z and out
+ * must not overlap.
+ */
+csl_status csl_apply(csl_plan* plan, const double* z, double* out);
+
+/*
+ * out = P^{-1} v for block-pair vectors (Eq. 4 via Section 2.3): each of the
+ * two interleaved blocks goes through the sine transform, the per-mode scale
+ * 1/sqrt((gamma mu + alpha)^2 + beta^2) and the inverse transform, in the
+ * plan's precision.  Because P acts identically on both blocks, a complex128
+ * vector may be passed as well.  v and out may be the same buffer.
+ */
+csl_status csl_precondition(csl_plan* plan, const double* v, double* out);
+
+/*
+ * Solve (K + lambda I) z = f (Eq. 1) by preconditioned MINRES on Eq. 2 with P
+ * (Eq. 4), zero initial guess, until the true relative residual is <= tol or
+ * maxit iterations.  f, z: complex128, M entries, may not overlap.  info may
+ * be NULL.  Returns CSL_OK, CSL_NOT_CONVERGED (z = last iterate),
+ * CSL_BREAKDOWN, or an argument/CUDA error.  Synchronises the plan's stream.
+ */
+csl_status csl_solve(csl_plan* plan, const double* f, double* z, double tol, int maxit,
+                     csl_solve_info* info);
+
+/*
+ * The same solve with HOST buffers: f_host is copied to the device, solved,
+ * and z copied back to z_host (pinned host memory gives full copy speed).
+ */
+csl_status csl_solve_host(csl_plan* plan, const double* f_host, double* z_host, double tol,
+                          int maxit, csl_solve_info* info);
+
+/*
+ * Adjoint solve (K + conj(lambda) I) y = g: the same preconditioned MINRES on
+ * the block system with beta -> -beta (A is symmetric, so this is the
+ * transposed system of Eq. 2 expressed in complex form; P is unchanged).
+ * With g = dL/dRe z + i dL/dIm z this gives y = dL/dRe f + i dL/dIm f.
+ */
+csl_status csl_adjoint(csl_plan* plan, const double* g, double* y, double tol, int maxit,
+                       csl_solve_info* info);
+
+/*
+ * Gradient of a loss with respect to the coefficient samples, given the
+ * solution z and the adjoint y (both complex128):
+ *   dL/da_e = -h_d^{-2} Re(conj(y_p - y_q) (z_p - z_q))
+ * for the face e between grid points p and q along axis d (values outside the
+ * grid are 0).  grad_faces[d] has the layout of coef_faces[d].  Derived from
+ * Eq. 2 by differentiating A x = r (the paper has no gradient).
+ */
+csl_status csl_coef_grad(csl_plan* plan, const double* z, const double* y,
+                         double* const grad_faces[3]);
+
+/*
+ * Measurement hook (not part of the method): time each kernel of one MINRES
+ * iteration on the plan's stream with CUDA events, `reps` launches each,
+ * against a scratch copy of the solver state so that no kernel exits early.
+ * The vectors hold whatever the last call left (run a solve first).  On
+ * return ms[i] is the mean duration of kernel i and names[i] its name, for
+ * i < *count (<= 8).  Synchronises the stream.
+ */
+csl_status csl_time_kernels(csl_plan* plan, int reps, double ms[8], const char* names[8], int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSL_H */

@@ -1,0 +1,277 @@
+"""ctypes binding of libcsl.so (include/csl.h).  Argument marshalling only:
+every step of the solve runs in the library's CUDA kernels.  Importing this
+module loads the library and raises if it has not been built."""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libcsl.so")
+
+OK, INVALID_ARG, UNSUPPORTED_SIZE, SINGULAR_PRECOND, BREAKDOWN, NOT_CONVERGED, TIMEOUT, CUDA_ERROR, \
+    OUT_OF_MEMORY = range(9)
+PREC_FP64, PREC_FP32 = 0, 1
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32}
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("gamma_override", ctypes.c_double),
+                ("lines_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double),
+                ("pnorm", ctypes.c_double), ("gamma", ctypes.c_double), ("checks", ctypes.c_int),
+                ("launches", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "csl_version": (ctypes.c_char_p, []),
+    "csl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "csl_last_error": (ctypes.c_char_p, []),
+    "csl_plan_options_init": (ctypes.c_int, [ctypes.POINTER(PlanOptions)]),
+    "csl_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(_P), ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(PlanOptions), _P]),
+    "csl_plan_destroy": (None, [_P]),
+    "csl_plan_set_stream": (ctypes.c_int, [_P, _P]),
+    "csl_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "csl_plan_gamma": (ctypes.c_double, [_P]),
+    "csl_apply": (ctypes.c_int, [_P, _P, _P]),
+    "csl_precondition": (ctypes.c_int, [_P, _P, _P]),
+    "csl_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+    "csl_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+    "csl_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+    "csl_coef_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "csl_time_kernels": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def load_library(path: str = LIBPATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libcsl.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(there is no fallback implementation)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load_library()
+
+
+class CSLError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = lib.csl_last_error().decode() if status in (CUDA_ERROR, OUT_OF_MEMORY) else ""
+        super().__init__(f"{where}: {status_string(status)}" + (f" [{detail}]" if detail else ""))
+
+
+def status_string(status: int) -> str:
+    return lib.csl_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return lib.csl_version().decode()
+
+
+def _check(status: int, where: str, allow=(OK,)):
+    if status not in allow:
+        raise CSLError(status, where)
+    return status
+
+
+@dataclass
+class Info:
+    iters: int
+    status: int
+    relres: float
+    pnorm: float
+    gamma: float
+    checks: int
+    launches: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+    @staticmethod
+    def from_c(ci: SolveInfo) -> "Info":
+        return Info(ci.iters, ci.status, ci.relres, ci.pnorm, ci.gamma, ci.checks, ci.launches)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dptr(t, dtype_names, what: str) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if str(t.dtype).replace("torch.", "") not in dtype_names:
+        raise ValueError(f"{what} must have dtype in {dtype_names}, got {t.dtype}")
+    return t.data_ptr()
+
+
+class Plan:
+    """A solver plan for one grid, coefficient field and shift lambda.
+
+    faces: (x-faces, y-faces[, z-faces]) float64 CUDA tensors in the layout of
+    include/csl.h (x fastest).  precision: "fp64" or "fp32" (FP32 sine
+    transforms and scale inside P^{-1}; everything else FP64).
+    """
+
+    def __init__(self, faces: Sequence, lam: complex, precision: str = "fp64",
+                 gamma: Optional[float] = None, lines_per_cta: int = 0, use_graph: bool = True,
+                 stream=None):
+        torch = _torch()
+        dim = len(faces)
+        if dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        fx = faces[0]
+        nx = fx.shape[-1] - 1
+        ny = fx.shape[-2]
+        nz = fx.shape[-3] if dim == 3 else 1
+        self.dim = dim
+        self.shape = (ny, nx) if dim == 2 else (nz, ny, nx)
+        self.M = nx * ny * nz
+        self.lam = complex(lam)
+        self._faces = [f.contiguous() for f in faces]
+        for i, f in enumerate(self._faces):
+            _dptr(f, ("float64",), f"faces[{i}]")
+        n = (ctypes.c_int64 * 3)(nx, ny, nz)
+        ptrs = (_P * 3)(*([f.data_ptr() for f in self._faces] + [None] * (3 - dim)))
+        opt = PlanOptions()
+        lib.csl_plan_options_init(ctypes.byref(opt))
+        opt.precision = _PREC[precision]
+        opt.gamma_override = float(gamma) if gamma is not None else float("nan")
+        opt.lines_per_cta = int(lines_per_cta)
+        opt.use_graph = 1 if use_graph else 0
+        self.precision = precision
+        h = _P()
+        st = lib.csl_plan_create(ctypes.byref(h), dim, n, ptrs, self.lam.real, self.lam.imag,
+                                 ctypes.byref(opt), _stream_handle(stream))
+        _check(st, "csl_plan_create")
+        self._h = h
+        self._faces = None  # the plan keeps its own copy
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.csl_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_stream(self, stream=None):
+        lib.csl_plan_set_stream(self._h, _stream_handle(stream))
+
+    @property
+    def gamma(self) -> float:
+        return lib.csl_plan_gamma(self._h)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return lib.csl_plan_workspace_bytes(self._h)
+
+    # -- operations ----------------------------------------------------------
+    def apply(self, z):
+        """(K + lambda I) z for a complex128 CUDA tensor of the grid's shape."""
+        torch = _torch()
+        self._sync_stream()
+        out = torch.empty_like(z)
+        _check(lib.csl_apply(self._h, _dptr(z, ("complex128",), "z"), out.data_ptr()), "csl_apply")
+        return out
+
+    def precondition(self, v):
+        """P^{-1} v for a complex128 (or (...,2) float64) CUDA tensor."""
+        torch = _torch()
+        self._sync_stream()
+        out = torch.empty_like(v)
+        _check(lib.csl_precondition(self._h, _dptr(v, ("complex128", "float64"), "v"), out.data_ptr()),
+               "csl_precondition")
+        return out
+
+    def solve(self, f, tol: float = 1e-8, maxit: int = 1000, out=None) -> Tuple[object, Info]:
+        torch = _torch()
+        self._sync_stream()
+        z = torch.empty_like(f) if out is None else out
+        ci = SolveInfo()
+        st = lib.csl_solve(self._h, _dptr(f, ("complex128",), "f"), _dptr(z, ("complex128",), "z"),
+                           float(tol), int(maxit), ctypes.byref(ci))
+        _check(st, "csl_solve", allow=(OK, NOT_CONVERGED, BREAKDOWN))
+        return z, Info.from_c(ci)
+
+    def adjoint(self, g, tol: float = 1e-8, maxit: int = 1000, out=None):
+        torch = _torch()
+        self._sync_stream()
+        y = torch.empty_like(g) if out is None else out
+        ci = SolveInfo()
+        st = lib.csl_adjoint(self._h, _dptr(g, ("complex128",), "g"), _dptr(y, ("complex128",), "y"),
+                             float(tol), int(maxit), ctypes.byref(ci))
+        _check(st, "csl_adjoint", allow=(OK, NOT_CONVERGED, BREAKDOWN))
+        return y, Info.from_c(ci)
+
+    def solve_host(self, f_host, z_host, tol: float = 1e-8, maxit: int = 1000) -> Info:
+        """Solve with host (CPU, ideally pinned) complex128 tensors/arrays."""
+        self._sync_stream()
+        ci = SolveInfo()
+        fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data
+        zp = z_host.data_ptr() if hasattr(z_host, "data_ptr") else z_host.ctypes.data
+        st = lib.csl_solve_host(self._h, fp, zp, float(tol), int(maxit), ctypes.byref(ci))
+        _check(st, "csl_solve_host", allow=(OK, NOT_CONVERGED, BREAKDOWN))
+        return Info.from_c(ci)
+
+    def time_kernels(self, reps: int = 10):
+        """{kernel name: mean ms per launch} for the kernels of one iteration
+        (measurement hook; run a solve first so the vectors hold real data)."""
+        self._sync_stream()
+        ms = (ctypes.c_double * 8)()
+        names = (ctypes.c_char_p * 8)()
+        cnt = ctypes.c_int(0)
+        _check(lib.csl_time_kernels(self._h, int(reps), ms, names, ctypes.byref(cnt)), "csl_time_kernels")
+        out = []
+        for i in range(cnt.value):
+            out.append((names[i].decode(), ms[i]))
+        return out
+
+    def coef_grad(self, z, y):
+        torch = _torch()
+        self._sync_stream()
+        nz, ny, nx = (1,) + self.shape if self.dim == 2 else self.shape
+        shapes = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][: self.dim]
+        grads = [torch.empty(s, dtype=torch.float64, device=z.device) for s in shapes]
+        if self.dim == 2:
+            grads = [g.reshape(s[1:]) for g, s in zip(grads, shapes)]
+        ptrs = (_P * 3)(*([g.data_ptr() for g in grads] + [None] * (3 - self.dim)))
+        _check(lib.csl_coef_grad(self._h, _dptr(z, ("complex128",), "z"), _dptr(y, ("complex128",), "y"),
+                                 ptrs), "csl_coef_grad")
+        return tuple(grads)

@@ -1,0 +1,945 @@
+// Host side of the C ABI declared in include/csl.h: plan set-up (Eq. 4 and
+// Section 2.3 tables), launch configurations, the MINRES driver (a CUDA graph
+// whose WHILE node is closed from the device when the true residual meets the
+// tolerance), and the remaining entry points.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/csl.h"
+#include "csl_kernels.cuh"
+
+using namespace csl;
+
+namespace {
+thread_local char g_last_error[512] = "";
+void record_error(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s failed at csl_api.cu:%d: %s (%s)", what, line,
+           cudaGetErrorName(e), cudaGetErrorString(e));
+}
+}  // namespace
+
+#define CSL_TRY(call)                                                               \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      record_error(e_, #call, __LINE__);                                            \
+      (void)cudaGetLastError();                                                     \
+      return e_ == cudaErrorMemoryAllocation ? CSL_OUT_OF_MEMORY : CSL_CUDA_ERROR; \
+    }                                                                               \
+  } while (0)
+#define CSL_NOTE(e, what) \
+  do {                    \
+    if ((e) != cudaSuccess) record_error((e), (what), __LINE__); \
+  } while (0)
+
+namespace {
+
+const int kSMs = 152;
+const int kMaxRedBlocks = 4096;
+const double kNaN = __builtin_nan("");
+
+struct PassCfg {
+  int logn = 0, n = 0, lines = 0, TL = 0, LS = 0, threads = 0, blocks = 0;
+  size_t smem = 0;
+  // strided geometry
+  int ncols = 0, nouter = 0;
+  long outer_stride = 0, line_stride = 0;
+};
+
+int ilog2_exact(long v) {
+  if (v <= 0 || (v & (v - 1))) return -1;
+  int l = 0;
+  while ((1L << l) < v) ++l;
+  return l;
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+struct csl_plan {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  long M = 0;
+  double h[3] = {1, 1, 1};
+  double alpha = 0, beta = 0, gamma = 0, amin = 0, amax = 0, sqrt_pmin = 0, sqrt_pmax = 0;
+  int precision = CSL_PREC_FP64;
+  int use_graph = 1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  // device memory
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double *cx = nullptr, *cy = nullptr, *cz = nullptr, *dg = nullptr, *stab = nullptr;
+  double* mu_d[3] = {nullptr, nullptr, nullptr};
+  float* mu_f[3] = {nullptr, nullptr, nullptr};
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* hs[3] = {nullptr, nullptr, nullptr};
+  double2 *b = nullptr, *x = nullptr, *io = nullptr;
+  double2* v[2] = {nullptr, nullptr};
+  double2* w[2] = {nullptr, nullptr};
+  void* z[2] = {nullptr, nullptr};
+  void* T = nullptr;
+  DevState* st = nullptr;
+  DevState* st_prof = nullptr;  // scratch state for csl_time_kernels
+  double* partials = nullptr;
+  unsigned long long* u64 = nullptr;
+  // launch configurations
+  PassCfg row, sy, sz;
+  int sten_blocks = 1, ew_blocks = 1;
+  double cnorm = 1;
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int graph_state = 0;  // 0 not built, 1 ready, -1 failed (host loop)
+};
+
+namespace {
+
+template <typename T>
+void* dalloc(csl_plan* P, size_t bytes, cudaError_t* err) {
+  void* p = nullptr;
+  if (*err != cudaSuccess) return nullptr;
+  *err = cudaMalloc(&p, bytes ? bytes : 16);
+  if (*err == cudaSuccess) {
+    P->allocs.push_back(p);
+    P->bytes += bytes;
+  }
+  return p;
+}
+
+void free_plan(csl_plan* P) {
+  if (!P) return;
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  for (void* p : P->allocs) cudaFree(p);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  delete P;
+}
+
+// ---- kernel attribute set-up (dynamic shared memory above 48 KB) ----------
+// dynamic shared memory limit of one kernel = opt-in maximum - its static shared memory
+cudaError_t allow_dyn_smem(const void* k) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+template <typename T>
+cudaError_t set_attrs_T() {
+  cudaError_t e = cudaSuccess;
+#define SETA(k) \
+  if (e == cudaSuccess) e = allow_dyn_smem((const void*)k)
+  SETA((k_row<T, LOAD_V, STORE_T>));
+  SETA((k_row<T, LOAD_LANCZOS, STORE_T>));
+  SETA((k_row<T, LOAD_T, STORE_Z>));
+  SETA((k_row<T, LOAD_T, STORE_Z_UPDATE>));
+  SETA((k_row<T, LOAD_T, STORE_D>));
+  SETA((k_strided<T, true>));
+  SETA((k_strided<T, false>));
+#undef SETA
+  return e;
+}
+
+cudaError_t set_attrs_once() {
+  static int done = 0;
+  static cudaError_t err = cudaSuccess;
+  if (!done) {
+    err = set_attrs_T<double>();
+    if (err == cudaSuccess) err = set_attrs_T<float>();
+    done = 1;
+  }
+  return err;
+}
+
+// ---- launch configuration -------------------------------------------------
+template <typename T>
+size_t smem_for(int lines, int LS, int logn) {
+  return dst_smem_bytes<T>(lines, LS, logn, 0);
+}
+
+template <typename T>
+void config_row(PassCfg& c, int n, int nrows) {
+  c.n = n;
+  c.logn = ilog2_exact(n + 1);
+  const int N = n + 1;
+  c.TL = N / 4 < 128 ? (N / 4 < 1 ? 1 : N / 4) : 128;
+  c.lines = 256 / c.TL;
+  c.LS = N + 1;
+  // keep the footprint within ~150 KB
+  while (c.lines > 1 && smem_for<T>(c.lines, c.LS, c.logn) > 150 * 1024) c.lines >>= 1;
+  c.threads = c.lines * c.TL;
+  c.smem = smem_for<T>(c.lines, c.LS, c.logn);
+  const long tiles = (nrows + c.lines - 1) / c.lines;
+  c.blocks = (int)(tiles < (long)kSMs * 8 ? tiles : (long)kSMs * 8);
+  c.ncols = n;
+  c.nouter = nrows;
+}
+
+template <typename T>
+void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride, long line_stride,
+                    int want_cols) {
+  c.n = n;
+  c.logn = ilog2_exact(n + 1);
+  const int N = n + 1;
+  c.LS = N + 1;
+  c.ncols = ncols;
+  c.nouter = nouter;
+  c.outer_stride = outer_stride;
+  c.line_stride = line_stride;
+  int C = want_cols > 0 ? next_pow2(want_cols) : (sizeof(T) == 8 ? 4 : 8);
+  const int cap_cols = next_pow2(ncols);
+  if (C > cap_cols) C = cap_cols;
+  int TL = N / 4 < 1 ? 1 : N / 4;
+  if (TL * C > 256) TL = 256 / C;
+  if (TL < 1) TL = 1;
+  // with short lines, take more columns per CTA to fill 256 threads
+  while (want_cols <= 0 && TL * C < 256 && C < cap_cols && smem_for<T>(2 * C, c.LS, c.logn) <= 150 * 1024)
+    C <<= 1;
+  while (C > 1 && smem_for<T>(C, c.LS, c.logn) > 200 * 1024) {
+    C >>= 1;
+  }
+  if (TL * C > 1024) TL = 1024 / C;
+  c.lines = C;
+  c.TL = TL;
+  c.threads = C * TL;
+  c.smem = smem_for<T>(C, c.LS, c.logn);
+  const long tiles = (long)((ncols + C - 1) / C) * nouter;
+  c.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
+}
+
+// ---- launches ---------------------------------------------------------------
+template <typename T>
+RowArgs<T> row_args(csl_plan* P) {
+  RowArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.logn = P->row.logn;
+  a.n = P->row.n;
+  a.nrows = P->row.nouter;
+  a.G = P->row.lines;
+  a.TL = P->row.TL;
+  a.LS = P->row.LS;
+  a.tw = (const typename C2<T>::t*)P->tw[0];
+  a.hs = (const T*)P->hs[0];
+  return a;
+}
+
+template <typename T, int LOAD, int STORE>
+void launch_row(csl_plan* P, const RowArgs<T>& a, cudaStream_t s) {
+  k_row<T, LOAD, STORE><<<P->row.blocks, P->row.threads, P->row.smem, s>>>(a);
+}
+
+template <typename T>
+StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
+  StridedArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.logn = c.logn;
+  a.n = c.n;
+  a.ncols = c.ncols;
+  a.nouter = c.nouter;
+  a.outer_stride = c.outer_stride;
+  a.line_stride = c.line_stride;
+  a.C = c.lines;
+  a.TL = c.TL;
+  a.LS = c.LS;
+  a.tw = (const typename C2<T>::t*)P->tw[axis];
+  a.hs = (const T*)P->hs[axis];
+  a.data = (typename C2<T>::t*)P->T;
+  return a;
+}
+
+template <typename T>
+void fill_mid(csl_plan* P, StridedArgs<T>& a, int axis) {
+  a.stab = (sizeof(T) == 8) ? P->stab : nullptr;
+  if (sizeof(T) == 4) {
+    a.mu_line = (const T*)P->mu_f[axis];
+    a.mu_col = (const T*)P->mu_f[0];
+    a.mu_outer = (axis == 2) ? (const T*)P->mu_f[1] : nullptr;
+  }
+  a.gamma = (T)P->gamma;
+  a.alpha = (T)P->alpha;
+  a.beta2 = (T)(P->beta * P->beta);
+  a.cnorm = (T)P->cnorm;
+  a.partials = P->partials;
+}
+
+// P^{-1} applied to the plan's T buffer after the x pass: [y fwd,] mid, [y inv]
+template <typename T>
+void launch_mid_chain(csl_plan* P, cudaStream_t s, DevState* st, int scalar_mode) {
+  if (P->dim == 2) {
+    StridedArgs<T> m = strided_args<T>(P, P->sy, 1);
+    fill_mid<T>(P, m, 1);
+    m.st = st;
+    m.scalar_mode = scalar_mode;
+    k_strided<T, true><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(m);
+  } else {
+    StridedArgs<T> y = strided_args<T>(P, P->sy, 1);
+    y.st = st;
+    k_strided<T, false><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(y);
+    StridedArgs<T> m = strided_args<T>(P, P->sz, 2);
+    fill_mid<T>(P, m, 2);
+    m.st = st;
+    m.scalar_mode = scalar_mode;
+    k_strided<T, true><<<P->sz.blocks, P->sz.threads, P->sz.smem, s>>>(m);
+    k_strided<T, false><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(y);
+  }
+}
+
+template <typename T>
+void launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  StencilArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g.nx = P->n[0];
+  a.g.ny = P->n[1];
+  a.g.nz = P->dim == 3 ? P->n[2] : 1;
+  a.g.M = P->M;
+  a.z = P->z[par];
+  a.vold = P->v[1 - par];
+  a.cx = P->cx;
+  a.cy = P->cy;
+  a.cz = P->cz;
+  a.dg = P->dg;
+  a.x = P->x;
+  a.b = P->b;
+  a.st = P->st;
+  a.partials = P->partials;
+  a.cond = P->cond;
+  a.use_cond = use_cond ? 1 : 0;
+  typedef typename C2<T>::t TZ;
+  if (P->dim == 2)
+    k_stencil<2, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
+  else
+    k_stencil<3, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
+}
+
+// one MINRES iteration with buffer parity `par` (v_j in v[par], z_j in z[par])
+template <typename T>
+void launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  launch_stencil<T>(P, par, s, use_cond);
+  RowArgs<T> r1 = row_args<T>(P);
+  r1.vnew = P->v[1 - par];
+  r1.vcur = P->v[par];
+  r1.tout = (typename C2<T>::t*)P->T;
+  r1.st = P->st;
+  launch_row<T, LOAD_LANCZOS, STORE_T>(P, r1, s);
+  launch_mid_chain<T>(P, s, P->st, 2);
+  RowArgs<T> r3 = row_args<T>(P);
+  r3.tin = (const typename C2<T>::t*)P->T;
+  r3.zout = (typename C2<T>::t*)P->z[1 - par];
+  r3.zcur = (const typename C2<T>::t*)P->z[par];
+  r3.wprev = P->w[par];
+  r3.wcur = P->w[1 - par];
+  r3.x = P->x;
+  r3.st = P->st;
+  launch_row<T, LOAD_T, STORE_Z_UPDATE>(P, r3, s);
+}
+
+void launch_iteration(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  if (P->precision == CSL_PREC_FP32)
+    launch_iteration_T<float>(P, par, s, use_cond);
+  else
+    launch_iteration_T<double>(P, par, s, use_cond);
+}
+
+// ingest f and compute z_1 = P^{-1} b, gamma_1
+template <typename T>
+void launch_prologue_T(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
+  IngestArgs ia;
+  memset(&ia, 0, sizeof(ia));
+  ia.M = P->M;
+  ia.f = f;
+  ia.b = P->b;
+  ia.v0 = P->v[0];
+  ia.v1 = P->v[1];
+  ia.w0 = P->w[0];
+  ia.w1 = P->w[1];
+  ia.x = P->x;
+  ia.st = P->st;
+  ia.partials = P->partials;
+  ia.tol = tol;
+  ia.beta = beta;
+  ia.maxit = maxit;
+  ia.sqrt_pmin = P->sqrt_pmin;
+  ia.sqrt_pmax = P->sqrt_pmax;
+  k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia);
+  RowArgs<T> r1 = row_args<T>(P);
+  r1.vin = P->v[0];
+  r1.tout = (typename C2<T>::t*)P->T;
+  r1.st = P->st;
+  launch_row<T, LOAD_V, STORE_T>(P, r1, s);
+  launch_mid_chain<T>(P, s, P->st, 1);
+  RowArgs<T> r3 = row_args<T>(P);
+  r3.tin = (const typename C2<T>::t*)P->T;
+  r3.zout = (typename C2<T>::t*)P->z[0];
+  r3.st = P->st;
+  launch_row<T, LOAD_T, STORE_Z>(P, r3, s);
+}
+
+void launch_prologue(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
+  if (P->precision == CSL_PREC_FP32)
+    launch_prologue_T<float>(P, f, tol, maxit, beta, s);
+  else
+    launch_prologue_T<double>(P, f, tol, maxit, beta, s);
+}
+
+template <typename T>
+void launch_precondition_T(csl_plan* P, const double2* v, double2* out, cudaStream_t s) {
+  RowArgs<T> r1 = row_args<T>(P);
+  r1.vin = v;
+  r1.tout = (typename C2<T>::t*)P->T;
+  launch_row<T, LOAD_V, STORE_T>(P, r1, s);
+  launch_mid_chain<T>(P, s, nullptr, 0);
+  RowArgs<T> r3 = row_args<T>(P);
+  r3.tin = (const typename C2<T>::t*)P->T;
+  r3.dout = out;
+  launch_row<T, LOAD_T, STORE_D>(P, r3, s);
+}
+
+// Build the graph: a single WHILE node whose body is two MINRES iterations
+// (both buffer parities).  The stencil kernel's last block sets the condition.
+csl_status build_graph(csl_plan* P) {
+  if (P->graph_state != 0) return CSL_OK;
+  P->graph_state = -1;
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) goto fail;
+  if (cudaGraphConditionalHandleCreate(&P->cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto fail;
+  {
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = P->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) goto fail;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      goto fail;
+    launch_iteration(P, 0, P->cap, true);
+    launch_iteration(P, 1, P->cap, true);
+    cudaGraph_t captured = body;
+    cudaError_t e = cudaStreamEndCapture(P->cap, &captured);
+    if (e != cudaSuccess) goto fail;
+    if (cudaGraphInstantiate(&P->gexec, g, 0) != cudaSuccess) goto fail;
+  }
+  P->graph = g;
+  P->graph_state = 1;
+  return CSL_OK;
+fail:
+  CSL_NOTE(cudaGetLastError(), "graph build (falling back to the host-driven loop)");
+  if (g) cudaGraphDestroy(g);
+  P->gexec = nullptr;
+  P->graph_state = -1;
+  return CSL_OK;  // the host-driven loop is used instead
+}
+
+csl_status run_loop(csl_plan* P, int maxit) {
+  if (P->use_graph) build_graph(P);
+  if (P->graph_state == 1) {
+    CSL_TRY(cudaGraphLaunch(P->gexec, P->stream));
+    return CSL_OK;
+  }
+  // host-driven loop: batches of 8 iterations, then read the done flag
+  int done = 0;
+  for (int it = 0; it < maxit + 4 && !done; it += 8) {
+    for (int k = 0; k < 8; ++k) launch_iteration(P, k & 1, P->stream, false);
+    CSL_TRY(cudaGetLastError());
+    CSL_TRY(cudaMemcpyAsync(&done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    CSL_TRY(cudaStreamSynchronize(P->stream));
+  }
+  return CSL_OK;
+}
+
+csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status) {
+  DevState h;
+  CSL_TRY(cudaMemcpyAsync(&h, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->stream));
+  CSL_TRY(cudaStreamSynchronize(P->stream));
+  *solve_status = (csl_status)h.status;
+  if (!h.done) *solve_status = CSL_NOT_CONVERGED;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->iters = h.iter;
+    info->status = (int)*solve_status;
+    info->relres = h.relres;
+    info->pnorm = h.eta_x;
+    info->gamma = P->gamma;
+    info->checks = h.checks;
+    // prologue kernels + every launched WHILE body (two iterations each)
+    const int per_iter = P->dim == 2 ? 4 : 6;
+    const int prologue = 1 + per_iter;
+    const int bodies = (h.loops + 1) / 2;
+    info->launches = prologue + (P->graph_state == 1 ? bodies * 2 * per_iter : h.loops * per_iter);
+  }
+  return CSL_OK;
+}
+
+csl_status solve_impl(csl_plan* P, const double* f, double* z, double tol, int maxit, csl_solve_info* info,
+                      double beta) {
+  if (!P || !f || !z) return CSL_INVALID_ARG;
+  if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
+  launch_prologue(P, (const double2*)f, tol, maxit, beta, P->stream);
+  CSL_TRY(cudaGetLastError());
+  csl_status s = run_loop(P, maxit);
+  if (s != CSL_OK) return s;
+  CSL_TRY(cudaMemcpyAsync(z, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  CSL_TRY(cudaGetLastError());
+  csl_status st = CSL_OK;
+  s = read_info(P, info, &st);
+  if (s != CSL_OK) return s;
+  return st;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* csl_version(void) { return "csl 0.1 (sm_103a)"; }
+
+const char* csl_last_error(void) { return g_last_error; }
+
+const char* csl_status_string(csl_status s) {
+  switch (s) {
+    case CSL_OK: return "CSL_OK";
+    case CSL_INVALID_ARG: return "CSL_INVALID_ARG";
+    case CSL_UNSUPPORTED_SIZE: return "CSL_UNSUPPORTED_SIZE";
+    case CSL_SINGULAR_PRECOND: return "CSL_SINGULAR_PRECOND";
+    case CSL_BREAKDOWN: return "CSL_BREAKDOWN";
+    case CSL_NOT_CONVERGED: return "CSL_NOT_CONVERGED";
+    case CSL_TIMEOUT: return "CSL_TIMEOUT";
+    case CSL_CUDA_ERROR: return "CSL_CUDA_ERROR";
+    case CSL_OUT_OF_MEMORY: return "CSL_OUT_OF_MEMORY";
+  }
+  return "CSL_UNKNOWN_STATUS";
+}
+
+csl_status csl_plan_options_init(csl_plan_options* opt) {
+  if (!opt) return CSL_INVALID_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = CSL_PREC_FP64;
+  opt->gamma_override = kNaN;
+  opt->lines_per_cta = 0;
+  opt->use_graph = 1;
+  return CSL_OK;
+}
+
+csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const double* const coef_faces[3],
+                           double alpha, double beta, const csl_plan_options* opt, void* stream) {
+  if (!out) return CSL_INVALID_ARG;
+  *out = nullptr;
+  if (!n || !coef_faces || (dim != 2 && dim != 3)) return CSL_INVALID_ARG;
+  if (!isfinite(alpha) || !isfinite(beta)) return CSL_INVALID_ARG;
+  for (int d = 0; d < dim; ++d) {
+    if (!coef_faces[d] || n[d] < 1) return CSL_INVALID_ARG;
+    if (n[d] + 1 < 4 || n[d] + 1 > 2048 || ilog2_exact(n[d] + 1) < 0) return CSL_UNSUPPORTED_SIZE;
+  }
+  csl_plan_options o;
+  csl_plan_options_init(&o);
+  if (opt) o = *opt;
+  if (o.precision != CSL_PREC_FP64 && o.precision != CSL_PREC_FP32) return CSL_INVALID_ARG;
+  CSL_TRY(set_attrs_once());
+
+  csl_plan* P = new (std::nothrow) csl_plan();
+  if (!P) return CSL_OUT_OF_MEMORY;
+  P->dim = dim;
+  P->precision = o.precision;
+  P->use_graph = o.use_graph;
+  P->stream = (cudaStream_t)stream;
+  P->alpha = alpha;
+  P->beta = beta;
+  P->M = 1;
+  for (int d = 0; d < 3; ++d) P->n[d] = d < dim ? (int)n[d] : 1;
+  for (int d = 0; d < dim; ++d) {
+    P->M *= n[d];
+    P->h[d] = 1.0 / (double)(n[d] + 1);
+  }
+  const long M = P->M;
+  const int nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  const size_t tsz = o.precision == CSL_PREC_FP32 ? sizeof(float) : sizeof(double);
+  long nface[3];
+  nface[0] = (long)nz * ny * (nx + 1);
+  nface[1] = (long)nz * (ny + 1) * nx;
+  nface[2] = dim == 3 ? (long)(nz + 1) * ny * nx : 0;
+
+  cudaError_t err = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
+  P->cx = (double*)dalloc<double>(P, nface[0] * 8, &err);
+  P->cy = (double*)dalloc<double>(P, nface[1] * 8, &err);
+  if (dim == 3) P->cz = (double*)dalloc<double>(P, nface[2] * 8, &err);
+  P->dg = (double*)dalloc<double>(P, M * 8, &err);
+  if (o.precision == CSL_PREC_FP64) P->stab = (double*)dalloc<double>(P, M * 8, &err);
+  for (int d = 0; d < dim; ++d) {
+    const int N = P->n[d] + 1;
+    P->mu_d[d] = (double*)dalloc<double>(P, (size_t)P->n[d] * 8, &err);
+    P->mu_f[d] = (float*)dalloc<float>(P, (size_t)P->n[d] * 4, &err);
+    P->tw[d] = dalloc<double>(P, (size_t)(N / 2) * 2 * tsz, &err);
+    P->hs[d] = dalloc<double>(P, (size_t)(N / 2 + 1) * tsz, &err);
+  }
+  P->b = (double2*)dalloc<double>(P, M * 16, &err);
+  P->x = (double2*)dalloc<double>(P, M * 16, &err);
+  P->io = (double2*)dalloc<double>(P, M * 16, &err);
+  for (int i = 0; i < 2; ++i) {
+    P->v[i] = (double2*)dalloc<double>(P, M * 16, &err);
+    P->w[i] = (double2*)dalloc<double>(P, M * 16, &err);
+    P->z[i] = dalloc<double>(P, M * 2 * tsz, &err);
+  }
+  P->T = dalloc<double>(P, M * 2 * tsz, &err);
+  P->st = (DevState*)dalloc<double>(P, sizeof(DevState), &err);
+  P->st_prof = (DevState*)dalloc<double>(P, sizeof(DevState), &err);
+  P->partials = (double*)dalloc<double>(P, (size_t)kMaxRedBlocks * 4 * 8, &err);
+  P->u64 = (unsigned long long*)dalloc<double>(P, 8 * 8, &err);
+  if (err != cudaSuccess) {
+    CSL_NOTE(err, "device allocation");
+    (void)cudaGetLastError();
+    free_plan(P);
+    return err == cudaErrorMemoryAllocation ? CSL_OUT_OF_MEMORY : CSL_CUDA_ERROR;
+  }
+  cudaStream_t s = P->stream;
+  P->ew_blocks = (int)((M + 255) / 256 < kSMs * 8 ? (M + 255) / 256 : kSMs * 8);
+  P->sten_blocks = P->ew_blocks;
+
+  // coefficient faces: a_e / h^2, min / max / validity (Eq. 1 and Eq. 4's a_min, a_max)
+  {
+    unsigned long long init[3] = {~0ull, 0ull, 0ull};
+    double* dst[3] = {P->cx, P->cy, P->cz};
+    double amin = INFINITY, amax = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      err = cudaMemcpyAsync(P->u64, init, sizeof(init), cudaMemcpyHostToDevice, s);
+      if (err == cudaSuccess) {
+        const long cnt = nface[d];
+        int blocks = (int)((cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024);
+        k_scale_faces<<<blocks, 256, 0, s>>>(coef_faces[d], dst[d], cnt, 1.0 / (P->h[d] * P->h[d]), P->u64);
+        err = cudaGetLastError();
+      }
+      unsigned long long res[3] = {0, 0, 0};
+      if (err == cudaSuccess) err = cudaMemcpyAsync(res, P->u64, sizeof(res), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err != cudaSuccess) {
+        CSL_NOTE(err, "coefficient set-up");
+        (void)cudaGetLastError();
+        free_plan(P);
+        return CSL_CUDA_ERROR;
+      }
+      if (res[2]) {
+        free_plan(P);
+        return CSL_INVALID_ARG;
+      }
+      double lo, hi;
+      memcpy(&lo, &res[0], 8);
+      memcpy(&hi, &res[1], 8);
+      amin = lo < amin ? lo : amin;
+      amax = hi > amax ? hi : amax;
+    }
+    P->amin = amin;
+    P->amax = amax;
+    P->gamma = (o.gamma_override > 0.0 && isfinite(o.gamma_override)) ? o.gamma_override : sqrt(amin * amax);
+  }
+  Grid g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.M = M;
+  if (dim == 2)
+    k_diag<2><<<P->ew_blocks, 256, 0, s>>>(g, P->cx, P->cy, P->cz, P->dg, alpha);
+  else
+    k_diag<3><<<P->ew_blocks, 256, 0, s>>>(g, P->cx, P->cy, P->cz, P->dg, alpha);
+
+  // Section 2.3 tables: 1D Laplacian eigenvalues, FFT twiddles, half sines
+  P->cnorm = 1.0;
+  for (int d = 0; d < dim; ++d) {
+    const int nd = P->n[d], N = nd + 1;
+    P->cnorm *= 2.0 / (double)N;
+    std::vector<double> mu(nd);
+    std::vector<float> muf(nd);
+    for (int k = 1; k <= nd; ++k) {
+      const double sn = sin(M_PI * (double)k / (2.0 * N));
+      mu[k - 1] = 4.0 / (P->h[d] * P->h[d]) * sn * sn;
+      muf[k - 1] = (float)mu[k - 1];
+    }
+    std::vector<double> twd(N), hsd(N / 2 + 1);
+    for (int m = 0; m < N / 2; ++m) {
+      twd[2 * m] = cos(2.0 * M_PI * (double)m / N);
+      twd[2 * m + 1] = -sin(2.0 * M_PI * (double)m / N);
+    }
+    for (int j = 0; j <= N / 2; ++j) hsd[j] = 0.5 * sin(M_PI * (double)j / N);
+    hsd[N / 2] = 0.5;
+    if (err == cudaSuccess) err = cudaMemcpy(P->mu_d[d], mu.data(), nd * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(P->mu_f[d], muf.data(), nd * 4, cudaMemcpyHostToDevice);
+    if (o.precision == CSL_PREC_FP32) {
+      std::vector<float> twf(N), hsf(N / 2 + 1);
+      for (int i = 0; i < N; ++i) twf[i] = (float)twd[i];
+      for (int j = 0; j <= N / 2; ++j) hsf[j] = (float)hsd[j];
+      if (err == cudaSuccess) err = cudaMemcpy(P->tw[d], twf.data(), N * 4, cudaMemcpyHostToDevice);
+      if (err == cudaSuccess) err = cudaMemcpy(P->hs[d], hsf.data(), (N / 2 + 1) * 4, cudaMemcpyHostToDevice);
+    } else {
+      if (err == cudaSuccess) err = cudaMemcpy(P->tw[d], twd.data(), N * 8, cudaMemcpyHostToDevice);
+      if (err == cudaSuccess) err = cudaMemcpy(P->hs[d], hsd.data(), (N / 2 + 1) * 8, cudaMemcpyHostToDevice);
+    }
+  }
+  // per-mode scale of P^{-1} (Eq. 4) and the extremes of its eigenvalues
+  if (err == cudaSuccess) {
+    unsigned long long init[2] = {~0ull, 0ull};
+    err = cudaMemcpyAsync(P->u64, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) {
+      if (dim == 2)
+        k_scale_table<2><<<P->ew_blocks, 256, 0, s>>>(g, P->mu_d[0], P->mu_d[1], nullptr, P->gamma, alpha, beta,
+                                                      P->cnorm, P->stab, P->u64);
+      else
+        k_scale_table<3><<<P->ew_blocks, 256, 0, s>>>(g, P->mu_d[0], P->mu_d[1], P->mu_d[2], P->gamma, alpha,
+                                                      beta, P->cnorm, P->stab, P->u64);
+      err = cudaGetLastError();
+    }
+    unsigned long long res[2] = {0, 0};
+    if (err == cudaSuccess) err = cudaMemcpyAsync(res, P->u64, sizeof(res), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(P->st, 0, sizeof(DevState), s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess) {
+      double qmin, qmax;
+      memcpy(&qmin, &res[0], 8);
+      memcpy(&qmax, &res[1], 8);
+      if (!(qmin > 0.0)) {
+        free_plan(P);
+        return CSL_SINGULAR_PRECOND;
+      }
+      P->sqrt_pmin = sqrt(sqrt(qmin));
+      P->sqrt_pmax = sqrt(sqrt(qmax));
+    }
+  }
+  if (err != cudaSuccess) {
+    CSL_NOTE(err, "table / scale set-up");
+    (void)cudaGetLastError();
+    free_plan(P);
+    return CSL_CUDA_ERROR;
+  }
+  // launch configurations of the sine-transform passes
+  if (o.precision == CSL_PREC_FP32) {
+    config_row<float>(P->row, nx, (int)(M / nx));
+    if (dim == 2) {
+      config_strided<float>(P->sy, ny, nx, 1, 0, nx, o.lines_per_cta);
+    } else {
+      config_strided<float>(P->sy, ny, nx, nz, (long)nx * ny, nx, o.lines_per_cta);
+      config_strided<float>(P->sz, nz, nx, ny, nx, (long)nx * ny, o.lines_per_cta);
+    }
+  } else {
+    config_row<double>(P->row, nx, (int)(M / nx));
+    if (dim == 2) {
+      config_strided<double>(P->sy, ny, nx, 1, 0, nx, o.lines_per_cta);
+    } else {
+      config_strided<double>(P->sy, ny, nx, nz, (long)nx * ny, nx, o.lines_per_cta);
+      config_strided<double>(P->sz, nz, nx, ny, nx, (long)nx * ny, o.lines_per_cta);
+    }
+  }
+  *out = P;
+  return CSL_OK;
+}
+
+void csl_plan_destroy(csl_plan* plan) {
+  if (!plan) return;
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+}
+
+csl_status csl_plan_set_stream(csl_plan* plan, void* stream) {
+  if (!plan) return CSL_INVALID_ARG;
+  plan->stream = (cudaStream_t)stream;
+  return CSL_OK;
+}
+
+size_t csl_plan_workspace_bytes(const csl_plan* plan) { return plan ? plan->bytes : 0; }
+
+double csl_plan_gamma(const csl_plan* plan) { return plan ? plan->gamma : kNaN; }
+
+csl_status csl_apply(csl_plan* P, const double* z, double* out) {
+  if (!P || !z || !out) return CSL_INVALID_ARG;
+  Grid g;
+  g.nx = P->n[0];
+  g.ny = P->n[1];
+  g.nz = P->dim == 3 ? P->n[2] : 1;
+  g.M = P->M;
+  if (P->dim == 2)
+    k_apply<2><<<P->ew_blocks, 256, 0, P->stream>>>(g, (const double2*)z, (double2*)out, P->cx, P->cy, P->cz,
+                                                    P->dg, P->beta);
+  else
+    k_apply<3><<<P->ew_blocks, 256, 0, P->stream>>>(g, (const double2*)z, (double2*)out, P->cx, P->cy, P->cz,
+                                                    P->dg, P->beta);
+  CSL_TRY(cudaGetLastError());
+  return CSL_OK;
+}
+
+csl_status csl_precondition(csl_plan* P, const double* v, double* out) {
+  if (!P || !v || !out) return CSL_INVALID_ARG;
+  if (P->precision == CSL_PREC_FP32)
+    launch_precondition_T<float>(P, (const double2*)v, (double2*)out, P->stream);
+  else
+    launch_precondition_T<double>(P, (const double2*)v, (double2*)out, P->stream);
+  CSL_TRY(cudaGetLastError());
+  return CSL_OK;
+}
+
+csl_status csl_solve(csl_plan* plan, const double* f, double* z, double tol, int maxit, csl_solve_info* info) {
+  if (!plan) return CSL_INVALID_ARG;
+  return solve_impl(plan, f, z, tol, maxit, info, plan->beta);
+}
+
+csl_status csl_adjoint(csl_plan* plan, const double* g, double* y, double tol, int maxit, csl_solve_info* info) {
+  if (!plan) return CSL_INVALID_ARG;
+  return solve_impl(plan, g, y, tol, maxit, info, -plan->beta);
+}
+
+csl_status csl_solve_host(csl_plan* P, const double* f_host, double* z_host, double tol, int maxit,
+                          csl_solve_info* info) {
+  if (!P || !f_host || !z_host) return CSL_INVALID_ARG;
+  if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
+  const size_t bytes = sizeof(double2) * P->M;
+  CSL_TRY(cudaMemcpyAsync(P->io, f_host, bytes, cudaMemcpyHostToDevice, P->stream));
+  launch_prologue(P, P->io, tol, maxit, P->beta, P->stream);
+  CSL_TRY(cudaGetLastError());
+  csl_status s = run_loop(P, maxit);
+  if (s != CSL_OK) return s;
+  CSL_TRY(cudaMemcpyAsync(z_host, P->x, bytes, cudaMemcpyDeviceToHost, P->stream));
+  csl_status st = CSL_OK;
+  s = read_info(P, info, &st);
+  if (s != CSL_OK) return s;
+  return st;
+}
+
+csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* const grad_faces[3]) {
+  if (!P || !z || !y || !grad_faces) return CSL_INVALID_ARG;
+  for (int d = 0; d < P->dim; ++d)
+    if (!grad_faces[d]) return CSL_INVALID_ARG;
+  Grid g;
+  g.nx = P->n[0];
+  g.ny = P->n[1];
+  g.nz = P->dim == 3 ? P->n[2] : 1;
+  g.M = P->M;
+  const double2* zz = (const double2*)z;
+  const double2* yy = (const double2*)y;
+  const int blocks = P->ew_blocks;
+  k_coef_grad<0><<<blocks, 256, 0, P->stream>>>(g, zz, yy, grad_faces[0], 1.0 / (P->h[0] * P->h[0]));
+  k_coef_grad<1><<<blocks, 256, 0, P->stream>>>(g, zz, yy, grad_faces[1], 1.0 / (P->h[1] * P->h[1]));
+  if (P->dim == 3)
+    k_coef_grad<2><<<blocks, 256, 0, P->stream>>>(g, zz, yy, grad_faces[2], 1.0 / (P->h[2] * P->h[2]));
+  CSL_TRY(cudaGetLastError());
+  return CSL_OK;
+}
+
+csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* names[8], int* count) {
+  if (!P || !ms || !names || !count || reps < 1) return CSL_INVALID_ARG;
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.gam = h.gam_old = h.gam1 = 1.0;
+  h.c = h.c_old = 1.0;
+  h.eta = h.eta_x = h.bnorm = 1.0;
+  h.tol = 1e-300;
+  h.maxit = 1 << 30;
+  h.beta = P->beta;
+  h.sqrt_pmin = h.sqrt_pmax = 0.0;
+  DevState* keep = P->st;
+  P->st = P->st_prof;  // all launches below read the scratch state
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  const bool fp32 = P->precision == CSL_PREC_FP32;
+  int k = 0;
+  const int nk = P->dim == 2 ? 4 : 6;
+  static const char* n2[4] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
+                              "k_row<LOAD_T,STORE_Z_UPDATE>"};
+  static const char* n3[6] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
+                              "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>"};
+  for (k = 0; k < nk && err == cudaSuccess; ++k) {
+    double tot = 0.0;
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+      err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
+      if (err != cudaSuccess) break;
+      err = cudaEventRecord(e0, P->stream);
+      if (err != cudaSuccess) break;
+      const int par = r & 1;
+      const bool last = (k == nk - 1);
+      if (k == 0) {
+        if (fp32) launch_stencil<float>(P, par, P->stream, false);
+        else launch_stencil<double>(P, par, P->stream, false);
+      } else if (k == 1) {
+        if (fp32) {
+          RowArgs<float> a = row_args<float>(P);
+          a.vnew = P->v[1 - par]; a.vcur = P->v[par]; a.tout = (float2*)P->T; a.st = P->st;
+          launch_row<float, LOAD_LANCZOS, STORE_T>(P, a, P->stream);
+        } else {
+          RowArgs<double> a = row_args<double>(P);
+          a.vnew = P->v[1 - par]; a.vcur = P->v[par]; a.tout = (double2*)P->T; a.st = P->st;
+          launch_row<double, LOAD_LANCZOS, STORE_T>(P, a, P->stream);
+        }
+      } else if (last) {
+        if (fp32) {
+          RowArgs<float> a = row_args<float>(P);
+          a.tin = (const float2*)P->T; a.zout = (float2*)P->z[1 - par]; a.zcur = (const float2*)P->z[par];
+          a.wprev = P->w[par]; a.wcur = P->w[1 - par]; a.x = P->x; a.st = P->st;
+          launch_row<float, LOAD_T, STORE_Z_UPDATE>(P, a, P->stream);
+        } else {
+          RowArgs<double> a = row_args<double>(P);
+          a.tin = (const double2*)P->T; a.zout = (double2*)P->z[1 - par]; a.zcur = (const double2*)P->z[par];
+          a.wprev = P->w[par]; a.wcur = P->w[1 - par]; a.x = P->x; a.st = P->st;
+          launch_row<double, LOAD_T, STORE_Z_UPDATE>(P, a, P->stream);
+        }
+      } else {
+        const bool mid = (P->dim == 2) || (k == 3);
+        const PassCfg& c = (P->dim == 2 || k != 3) ? P->sy : P->sz;
+        const int axis = (P->dim == 2 || k != 3) ? 1 : 2;
+        if (fp32) {
+          StridedArgs<float> a = strided_args<float>(P, c, axis);
+          a.st = P->st;
+          if (mid) {
+            fill_mid<float>(P, a, axis);
+            a.scalar_mode = 2;
+            k_strided<float, true><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
+          } else {
+            k_strided<float, false><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
+          }
+        } else {
+          StridedArgs<double> a = strided_args<double>(P, c, axis);
+          a.st = P->st;
+          if (mid) {
+            fill_mid<double>(P, a, axis);
+            a.scalar_mode = 2;
+            k_strided<double, true><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
+          } else {
+            k_strided<double, false><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
+          }
+        }
+      }
+      err = cudaGetLastError();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, P->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+      tot += t;
+    }
+    ms[k] = tot / reps;
+    names[k] = P->dim == 2 ? n2[k] : n3[k];
+  }
+  P->st = keep;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  *count = k;
+  if (err != cudaSuccess) {
+    record_error(err, "csl_time_kernels", __LINE__);
+    (void)cudaGetLastError();
+    return CSL_CUDA_ERROR;
+  }
+  return CSL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Shared device types for the complex-shifted Laplacian solver (arXiv 2408.00488).
+//
+// Vector layout in HBM: one 16-byte double2 per grid point holding the pair
+// (block-1, block-2) of the 2x2 block real system of Eq. 2, C order with x
+// fastest.  Both blocks always travel together, so every sine transform is a
+// complex FFT of the pair and every stencil load serves both blocks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace csl {
+
+template <typename T> struct C2;
+template <> struct C2<double> { typedef double2 t; };
+template <> struct C2<float> { typedef float2 t; };
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t mkc(T x, T y) {
+  typename C2<T>::t r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+template <typename T> __device__ __forceinline__ typename C2<T>::t from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+template <typename TZ> __device__ __forceinline__ TZ store_as(double2 v);
+template <> __device__ __forceinline__ double2 store_as<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 store_as<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+
+// Scalars of one MINRES solve, resident in device memory so that the whole
+// iteration (including the Givens step and the stopping decision) runs
+// without host round trips.
+struct DevState {
+  // Lanczos recurrence: gam = gamma_j, gam_old = gamma_{j-1}, delta = delta_j
+  double gam, gam_old, gam1, delta;
+  // Givens rotations (c_j, c_{j-1}, s_j, s_{j-1}) and the rotated right-hand side eta
+  double c, c_old, s, s_old, eta;
+  // coefficients of the fused update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1}
+  double w_a, w_b, w_c, x_coef;
+  double bnorm, tol;
+  double rho;     // calibrated ratio ||b - A x||_2 / |eta| (residual 2-norm per P^{-1}-norm)
+  double relres;  // last explicitly evaluated true relative residual
+  double eta_x;   // |eta| belonging to the current iterate x
+  double beta;    // coupling coefficient of this solve (beta, or -beta for the adjoint)
+  double sqrt_pmin, sqrt_pmax;  // sqrt of extreme eigenvalues of one block of P
+  int iter;       // completed iterations = index of the current iterate x
+  int maxit, done, status, check, lucky, checks, calibrated, loops;
+  unsigned int tickets[4];
+};
+
+enum { TICKET_STENCIL = 0, TICKET_MID = 1, TICKET_INGEST = 2, TICKET_AUX = 3 };
+
+// status codes mirrored from csl.h
+enum {
+  ST_OK = 0, ST_INVALID_ARG = 1, ST_UNSUPPORTED = 2, ST_SINGULAR = 3, ST_BREAKDOWN = 4,
+  ST_NOT_CONVERGED = 5, ST_TIMEOUT = 6, ST_CUDA = 7, ST_OOM = 8
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV per-thread values over the block; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*NV */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid * NV + i] = v[i];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = (lane < nw) ? sh[lane * NV + i] : 0.0;
+      v[i] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic grid reduction: every block deposits its block sum in
+// partials[blockIdx.x*NV + i]; the last block to arrive (atomic ticket) sums
+// the deposits in block order and returns true with the totals in tot[]
+// (valid in all threads of that block).  The ticket is re-armed for reuse.
+template <int NV>
+__device__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned int* ticket,
+                                    double (&tot)[NV]) {
+  __shared__ double sh[32 * NV];
+  __shared__ int s_last;
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) partials[blockIdx.x * NV + i] = v[i];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[b * NV + i];
+  }
+  block_sum<NV>(acc, sh);
+  __shared__ double s_tot[NV];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s_tot[i] = acc[i];
+    *ticket = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) tot[i] = s_tot[i];
+  return true;
+}
+
+}  // namespace csl
