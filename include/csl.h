@@ -21,7 +21,7 @@
  * Conventions shared by every entry point
  *  - Grids: dim = 2 or 3; n[0], n[1], n[2] are the interior point counts along
  *    x, y, z (n[2] ignored for dim = 2).  Every n[d] + 1 must be a power of two
- *    between 4 and 2048 (else CSL_UNSUPPORTED_SIZE).
+ *    between 4 and 1024 (else CSL_UNSUPPORTED_SIZE).
  *  - Grid vectors are C-order arrays with x fastest: point (ix, iy[, iz]) at
  *    index ix + n[0]*(iy + n[1]*iz).  "complex128" vectors hold interleaved
  *    (re, im) doubles; "block-pair" vectors hold (block-1, block-2) doubles of
@@ -51,7 +51,7 @@ extern "C" {
 typedef enum csl_status {
   CSL_OK = 0,
   CSL_INVALID_ARG = 1,       /* null pointer, dim not 2/3, n < 1, non-finite shift, coefficient <= 0 */
-  CSL_UNSUPPORTED_SIZE = 2,  /* n[d] + 1 not a power of two in [4, 2048] */
+  CSL_UNSUPPORTED_SIZE = 2,  /* n[d] + 1 not a power of two in [4, 1024] */
   CSL_SINGULAR_PRECOND = 3,  /* some (gamma mu_k + alpha)^2 + beta^2 == 0 (only possible when beta == 0) */
   CSL_BREAKDOWN = 4,         /* non-finite or negative <P^{-1} v, v> in the Lanczos process */
   CSL_NOT_CONVERGED = 5,     /* maxit reached; z holds the last iterate, info is filled */

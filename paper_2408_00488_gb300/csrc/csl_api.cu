@@ -1,7 +1,7 @@
 // Host side of the C ABI declared in include/csl.h: plan set-up (Eq. 4 and
-// Section 2.3 tables), launch configurations, the MINRES driver (a CUDA graph
-// whose WHILE node is closed from the device when the true residual meets the
-// tolerance), and the remaining entry points.
+// the Section 2.3 tables), launch configurations, the MINRES driver (a CUDA
+// graph whose WHILE node is closed from the device once the true residual
+// meets the tolerance), and the remaining entry points.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -11,6 +11,7 @@
 
 #include "../../include/csl.h"
 #include "csl_kernels.cuh"
+#include "csl_passes.cuh"
 
 using namespace csl;
 
@@ -31,8 +32,8 @@ void record_error(cudaError_t e, const char* what, int line) {
       return e_ == cudaErrorMemoryAllocation ? CSL_OUT_OF_MEMORY : CSL_CUDA_ERROR; \
     }                                                                               \
   } while (0)
-#define CSL_NOTE(e, what) \
-  do {                    \
+#define CSL_NOTE(e, what)                                        \
+  do {                                                           \
     if ((e) != cudaSuccess) record_error((e), (what), __LINE__); \
   } while (0)
 
@@ -42,12 +43,12 @@ const int kSMs = 152;
 const int kMaxRedBlocks = 4096;
 const double kNaN = __builtin_nan("");
 
+// one sine-transform pass: line length N = n + 1, CTA shape and grid
 struct PassCfg {
-  int logn = 0, n = 0, lines = 0, TL = 0, LS = 0, threads = 0, blocks = 0;
-  size_t smem = 0;
-  // strided geometry
-  int ncols = 0, nouter = 0;
+  int N = 0, n = 0, lines = 0;  // lines per CTA
+  int ncols = 0, nouter = 0;     // strided: x extent and outer blocks; row: nouter = rows
   long outer_stride = 0, line_stride = 0;
+  PassLaunch L = {1, 32, 0};
 };
 
 int ilog2_exact(long v) {
@@ -55,12 +56,6 @@ int ilog2_exact(long v) {
   int l = 0;
   while ((1L << l) < v) ++l;
   return l;
-}
-
-int next_pow2(int v) {
-  int p = 1;
-  while (p < v) p <<= 1;
-  return p;
 }
 
 }  // namespace
@@ -75,7 +70,6 @@ struct csl_plan {
   int use_graph = 1;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
-  // device memory
   std::vector<void*> allocs;
   size_t bytes = 0;
   double *cx = nullptr, *cy = nullptr, *cz = nullptr, *dg = nullptr, *stab = nullptr;
@@ -92,20 +86,17 @@ struct csl_plan {
   DevState* st_prof = nullptr;  // scratch state for csl_time_kernels
   double* partials = nullptr;
   unsigned long long* u64 = nullptr;
-  // launch configurations
   PassCfg row, sy, sz;
   int sten_blocks = 1, ew_blocks = 1;
   double cnorm = 1;
-  // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
-  int graph_state = 0;  // 0 not built, 1 ready, -1 failed (host loop)
+  int graph_state = 0;  // 0 not built, 1 ready, -1 failed (host-driven loop)
 };
 
 namespace {
 
-template <typename T>
 void* dalloc(csl_plan* P, size_t bytes, cudaError_t* err) {
   void* p = nullptr;
   if (*err != cudaSuccess) return nullptr;
@@ -126,100 +117,70 @@ void free_plan(csl_plan* P) {
   delete P;
 }
 
-// ---- kernel attribute set-up (dynamic shared memory above 48 KB) ----------
-// dynamic shared memory limit of one kernel = opt-in maximum - its static shared memory
-cudaError_t allow_dyn_smem(const void* k) {
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  return e;
-}
-
-template <typename T>
-cudaError_t set_attrs_T() {
-  cudaError_t e = cudaSuccess;
-#define SETA(k) \
-  if (e == cudaSuccess) e = allow_dyn_smem((const void*)k)
-  SETA((k_row<T, LOAD_V, STORE_T>));
-  SETA((k_row<T, LOAD_LANCZOS, STORE_T>));
-  SETA((k_row<T, LOAD_T, STORE_Z>));
-  SETA((k_row<T, LOAD_T, STORE_Z_UPDATE>));
-  SETA((k_row<T, LOAD_T, STORE_D>));
-  SETA((k_strided<T, true>));
-  SETA((k_strided<T, false>));
-#undef SETA
-  return e;
-}
-
 cudaError_t set_attrs_once() {
   static int done = 0;
   static cudaError_t err = cudaSuccess;
   if (!done) {
-    err = set_attrs_T<double>();
-    if (err == cudaSuccess) err = set_attrs_T<float>();
+    err = set_pass_attrs<double>();
+    if (err == cudaSuccess) err = set_pass_attrs<float>();
     done = 1;
   }
   return err;
 }
 
 // ---- launch configuration -------------------------------------------------
+// CTA of `threads` lanes holds threads/TPL lines; shrink the CTA until its
+// shared memory fits ~100 KB (two or more CTAs per SM).
 template <typename T>
-size_t smem_for(int lines, int LS, int logn) {
-  return dst_smem_bytes<T>(lines, LS, logn, 0);
+void choose_cta(PassCfg& c, int want_threads) {
+  const int tpl = pass_tpl(c.N);
+  int threads = want_threads;
+  while (threads > 32 && pass_smem<T>(c.N, threads / tpl) > 100 * 1024) threads >>= 1;
+  c.lines = threads / tpl;
+  c.L.threads = threads;
+  c.L.smem = pass_smem<T>(c.N, c.lines);
 }
 
 template <typename T>
 void config_row(PassCfg& c, int n, int nrows) {
   c.n = n;
-  c.logn = ilog2_exact(n + 1);
-  const int N = n + 1;
-  c.TL = N / 4 < 128 ? (N / 4 < 1 ? 1 : N / 4) : 128;
-  c.lines = 256 / c.TL;
-  c.LS = N + 1;
-  // keep the footprint within ~150 KB
-  while (c.lines > 1 && smem_for<T>(c.lines, c.LS, c.logn) > 150 * 1024) c.lines >>= 1;
-  c.threads = c.lines * c.TL;
-  c.smem = smem_for<T>(c.lines, c.LS, c.logn);
-  const long tiles = (nrows + c.lines - 1) / c.lines;
-  c.blocks = (int)(tiles < (long)kSMs * 8 ? tiles : (long)kSMs * 8);
-  c.ncols = n;
+  c.N = n + 1;
   c.nouter = nrows;
+  c.ncols = n;
+  int threads = 256;
+  const int tpl = pass_tpl(c.N);
+  // few rows: smaller CTAs so that every SM gets work
+  while (threads > 32 && threads / tpl > 1 && (nrows + threads / tpl - 1) / (threads / tpl) < 2 * kSMs) threads >>= 1;
+  choose_cta<T>(c, threads);
+  const long tiles = (nrows + c.lines - 1) / c.lines;
+  c.L.blocks = (int)(tiles < (long)kSMs * 16 ? tiles : (long)kSMs * 16);
 }
 
 template <typename T>
-void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride, long line_stride,
-                    int want_cols) {
+void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride, long line_stride, int want_lines) {
   c.n = n;
-  c.logn = ilog2_exact(n + 1);
-  const int N = n + 1;
-  c.LS = N + 1;
+  c.N = n + 1;
   c.ncols = ncols;
   c.nouter = nouter;
   c.outer_stride = outer_stride;
   c.line_stride = line_stride;
-  int C = want_cols > 0 ? next_pow2(want_cols) : (sizeof(T) == 8 ? 4 : 8);
-  const int cap_cols = next_pow2(ncols);
-  if (C > cap_cols) C = cap_cols;
-  int TL = N / 4 < 1 ? 1 : N / 4;
-  if (TL * C > 256) TL = 256 / C;
-  if (TL < 1) TL = 1;
-  // with short lines, take more columns per CTA to fill 256 threads
-  while (want_cols <= 0 && TL * C < 256 && C < cap_cols && smem_for<T>(2 * C, c.LS, c.logn) <= 150 * 1024)
-    C <<= 1;
-  while (C > 1 && smem_for<T>(C, c.LS, c.logn) > 200 * 1024) {
-    C >>= 1;
+  const int tpl = pass_tpl(c.N);
+  int threads = 256;
+  if (want_lines > 0) {
+    int l = 1;
+    while (l < want_lines) l <<= 1;
+    threads = l * tpl < 32 ? 32 : l * tpl;
+    if (threads > 1024) threads = 1024;
   }
-  if (TL * C > 1024) TL = 1024 / C;
-  c.lines = C;
-  c.TL = TL;
-  c.threads = C * TL;
-  c.smem = smem_for<T>(C, c.LS, c.logn);
-  const long tiles = (long)((ncols + C - 1) / C) * nouter;
-  c.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
+  // no wider than the grid's x extent needs
+  while (threads > 32 && (threads / tpl) / 2 >= ncols) threads >>= 1;
+  // few tiles: smaller CTAs so that every SM gets work
+  while (want_lines <= 0 && threads > 32 && threads / tpl > 2 &&
+         (long)((ncols + threads / tpl - 1) / (threads / tpl)) * nouter < 2 * kSMs)
+    threads >>= 1;
+  choose_cta<T>(c, threads);
+  const long tiles = (long)((ncols + c.lines - 1) / c.lines) * nouter;
+  c.L.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
 }
 
 // ---- launches ---------------------------------------------------------------
@@ -227,35 +188,22 @@ template <typename T>
 RowArgs<T> row_args(csl_plan* P) {
   RowArgs<T> a;
   memset(&a, 0, sizeof(a));
-  a.logn = P->row.logn;
   a.n = P->row.n;
   a.nrows = P->row.nouter;
-  a.G = P->row.lines;
-  a.TL = P->row.TL;
-  a.LS = P->row.LS;
   a.tw = (const typename C2<T>::t*)P->tw[0];
   a.hs = (const T*)P->hs[0];
   return a;
-}
-
-template <typename T, int LOAD, int STORE>
-void launch_row(csl_plan* P, const RowArgs<T>& a, cudaStream_t s) {
-  k_row<T, LOAD, STORE><<<P->row.blocks, P->row.threads, P->row.smem, s>>>(a);
 }
 
 template <typename T>
 StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
   StridedArgs<T> a;
   memset(&a, 0, sizeof(a));
-  a.logn = c.logn;
   a.n = c.n;
   a.ncols = c.ncols;
   a.nouter = c.nouter;
   a.outer_stride = c.outer_stride;
   a.line_stride = c.line_stride;
-  a.C = c.lines;
-  a.TL = c.TL;
-  a.LS = c.LS;
   a.tw = (const typename C2<T>::t*)P->tw[axis];
   a.hs = (const T*)P->hs[axis];
   a.data = (typename C2<T>::t*)P->T;
@@ -277,30 +225,37 @@ void fill_mid(csl_plan* P, StridedArgs<T>& a, int axis) {
   a.partials = P->partials;
 }
 
+template <typename T>
+cudaError_t run_row(csl_plan* P, int load, int store, const RowArgs<T>& a, cudaStream_t s) {
+  return launch_row<T>(P->row.N, load, store, a, P->row.L, s);
+}
+
 // P^{-1} applied to the plan's T buffer after the x pass: [y fwd,] mid, [y inv]
 template <typename T>
-void launch_mid_chain(csl_plan* P, cudaStream_t s, DevState* st, int scalar_mode) {
+cudaError_t launch_mid_chain(csl_plan* P, cudaStream_t s, DevState* st, int scalar_mode) {
+  cudaError_t e;
   if (P->dim == 2) {
     StridedArgs<T> m = strided_args<T>(P, P->sy, 1);
     fill_mid<T>(P, m, 1);
     m.st = st;
     m.scalar_mode = scalar_mode;
-    k_strided<T, true><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(m);
-  } else {
-    StridedArgs<T> y = strided_args<T>(P, P->sy, 1);
-    y.st = st;
-    k_strided<T, false><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(y);
-    StridedArgs<T> m = strided_args<T>(P, P->sz, 2);
-    fill_mid<T>(P, m, 2);
-    m.st = st;
-    m.scalar_mode = scalar_mode;
-    k_strided<T, true><<<P->sz.blocks, P->sz.threads, P->sz.smem, s>>>(m);
-    k_strided<T, false><<<P->sy.blocks, P->sy.threads, P->sy.smem, s>>>(y);
+    return launch_strided<T>(P->sy.N, true, m, P->sy.L, s);
   }
+  StridedArgs<T> y = strided_args<T>(P, P->sy, 1);
+  y.st = st;
+  e = launch_strided<T>(P->sy.N, false, y, P->sy.L, s);
+  if (e != cudaSuccess) return e;
+  StridedArgs<T> m = strided_args<T>(P, P->sz, 2);
+  fill_mid<T>(P, m, 2);
+  m.st = st;
+  m.scalar_mode = scalar_mode;
+  e = launch_strided<T>(P->sz.N, true, m, P->sz.L, s);
+  if (e != cudaSuccess) return e;
+  return launch_strided<T>(P->sy.N, false, y, P->sy.L, s);
 }
 
 template <typename T>
-void launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
   StencilArgs a;
   memset(&a, 0, sizeof(a));
   a.g.nx = P->n[0];
@@ -324,40 +279,50 @@ void launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
     k_stencil<2, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
   else
     k_stencil<3, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+RowArgs<T> p1_args(csl_plan* P, int par) {
+  RowArgs<T> r = row_args<T>(P);
+  r.vnew = P->v[1 - par];
+  r.vcur = P->v[par];
+  r.tout = (typename C2<T>::t*)P->T;
+  r.st = P->st;
+  return r;
+}
+
+template <typename T>
+RowArgs<T> p3_args(csl_plan* P, int par) {
+  RowArgs<T> r = row_args<T>(P);
+  r.tin = (const typename C2<T>::t*)P->T;
+  r.zout = (typename C2<T>::t*)P->z[1 - par];
+  r.zcur = (const typename C2<T>::t*)P->z[par];
+  r.wprev = P->w[par];
+  r.wcur = P->w[1 - par];
+  r.x = P->x;
+  r.st = P->st;
+  return r;
 }
 
 // one MINRES iteration with buffer parity `par` (v_j in v[par], z_j in z[par])
 template <typename T>
-void launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
-  launch_stencil<T>(P, par, s, use_cond);
-  RowArgs<T> r1 = row_args<T>(P);
-  r1.vnew = P->v[1 - par];
-  r1.vcur = P->v[par];
-  r1.tout = (typename C2<T>::t*)P->T;
-  r1.st = P->st;
-  launch_row<T, LOAD_LANCZOS, STORE_T>(P, r1, s);
-  launch_mid_chain<T>(P, s, P->st, 2);
-  RowArgs<T> r3 = row_args<T>(P);
-  r3.tin = (const typename C2<T>::t*)P->T;
-  r3.zout = (typename C2<T>::t*)P->z[1 - par];
-  r3.zcur = (const typename C2<T>::t*)P->z[par];
-  r3.wprev = P->w[par];
-  r3.wcur = P->w[1 - par];
-  r3.x = P->x;
-  r3.st = P->st;
-  launch_row<T, LOAD_T, STORE_Z_UPDATE>(P, r3, s);
+cudaError_t launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  cudaError_t e = launch_stencil<T>(P, par, s, use_cond);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, par), s);
+  if (e == cudaSuccess) e = launch_mid_chain<T>(P, s, P->st, 2);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, par), s);
+  return e;
 }
 
-void launch_iteration(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
-  if (P->precision == CSL_PREC_FP32)
-    launch_iteration_T<float>(P, par, s, use_cond);
-  else
-    launch_iteration_T<double>(P, par, s, use_cond);
+cudaError_t launch_iteration(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  if (P->precision == CSL_PREC_FP32) return launch_iteration_T<float>(P, par, s, use_cond);
+  return launch_iteration_T<double>(P, par, s, use_cond);
 }
 
 // ingest f and compute z_1 = P^{-1} b, gamma_1
 template <typename T>
-void launch_prologue_T(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
+cudaError_t launch_prologue_T(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
   IngestArgs ia;
   memset(&ia, 0, sizeof(ia));
   ia.M = P->M;
@@ -376,74 +341,77 @@ void launch_prologue_T(csl_plan* P, const double2* f, double tol, int maxit, dou
   ia.sqrt_pmin = P->sqrt_pmin;
   ia.sqrt_pmax = P->sqrt_pmax;
   k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia);
+  cudaError_t e = cudaGetLastError();
   RowArgs<T> r1 = row_args<T>(P);
   r1.vin = P->v[0];
   r1.tout = (typename C2<T>::t*)P->T;
   r1.st = P->st;
-  launch_row<T, LOAD_V, STORE_T>(P, r1, s);
-  launch_mid_chain<T>(P, s, P->st, 1);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_V, STORE_T, r1, s);
+  if (e == cudaSuccess) e = launch_mid_chain<T>(P, s, P->st, 1);
   RowArgs<T> r3 = row_args<T>(P);
   r3.tin = (const typename C2<T>::t*)P->T;
   r3.zout = (typename C2<T>::t*)P->z[0];
   r3.st = P->st;
-  launch_row<T, LOAD_T, STORE_Z>(P, r3, s);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z, r3, s);
+  return e;
 }
 
-void launch_prologue(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
-  if (P->precision == CSL_PREC_FP32)
-    launch_prologue_T<float>(P, f, tol, maxit, beta, s);
-  else
-    launch_prologue_T<double>(P, f, tol, maxit, beta, s);
+cudaError_t launch_prologue(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
+  if (P->precision == CSL_PREC_FP32) return launch_prologue_T<float>(P, f, tol, maxit, beta, s);
+  return launch_prologue_T<double>(P, f, tol, maxit, beta, s);
 }
 
 template <typename T>
-void launch_precondition_T(csl_plan* P, const double2* v, double2* out, cudaStream_t s) {
+cudaError_t launch_precondition_T(csl_plan* P, const double2* v, double2* out, cudaStream_t s) {
   RowArgs<T> r1 = row_args<T>(P);
   r1.vin = v;
   r1.tout = (typename C2<T>::t*)P->T;
-  launch_row<T, LOAD_V, STORE_T>(P, r1, s);
-  launch_mid_chain<T>(P, s, nullptr, 0);
+  cudaError_t e = run_row<T>(P, LOAD_V, STORE_T, r1, s);
+  if (e == cudaSuccess) e = launch_mid_chain<T>(P, s, nullptr, 0);
   RowArgs<T> r3 = row_args<T>(P);
   r3.tin = (const typename C2<T>::t*)P->T;
   r3.dout = out;
-  launch_row<T, LOAD_T, STORE_D>(P, r3, s);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_D, r3, s);
+  return e;
 }
 
-// Build the graph: a single WHILE node whose body is two MINRES iterations
-// (both buffer parities).  The stencil kernel's last block sets the condition.
-csl_status build_graph(csl_plan* P) {
-  if (P->graph_state != 0) return CSL_OK;
+// Build the graph: one WHILE node whose body is two MINRES iterations (both
+// buffer parities); the stencil kernel's last block sets the condition.
+void build_graph(csl_plan* P) {
+  if (P->graph_state != 0) return;
   P->graph_state = -1;
   cudaGraph_t g = nullptr;
-  if (cudaGraphCreate(&g, 0) != cudaSuccess) goto fail;
-  if (cudaGraphConditionalHandleCreate(&P->cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto fail;
-  {
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&P->cond, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
     cp.conditional.handle = P->cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) goto fail;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
-        cudaSuccess)
-      goto fail;
-    launch_iteration(P, 0, P->cap, true);
-    launch_iteration(P, 1, P->cap, true);
-    cudaGraph_t captured = body;
-    cudaError_t e = cudaStreamEndCapture(P->cap, &captured);
-    if (e != cudaSuccess) goto fail;
-    if (cudaGraphInstantiate(&P->gexec, g, 0) != cudaSuccess) goto fail;
+    e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_iteration(P, 0, P->cap, true);
+      if (e1 == cudaSuccess) e1 = launch_iteration(P, 1, P->cap, true);
+      cudaGraph_t captured = body;
+      e = cudaStreamEndCapture(P->cap, &captured);
+      if (e == cudaSuccess) e = e1;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->gexec, g, 0);
+  if (e != cudaSuccess) {
+    CSL_NOTE(e, "graph build (falling back to the host-driven loop)");
+    (void)cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    P->gexec = nullptr;
+    return;
   }
   P->graph = g;
   P->graph_state = 1;
-  return CSL_OK;
-fail:
-  CSL_NOTE(cudaGetLastError(), "graph build (falling back to the host-driven loop)");
-  if (g) cudaGraphDestroy(g);
-  P->gexec = nullptr;
-  P->graph_state = -1;
-  return CSL_OK;  // the host-driven loop is used instead
 }
 
 csl_status run_loop(csl_plan* P, int maxit) {
@@ -455,8 +423,7 @@ csl_status run_loop(csl_plan* P, int maxit) {
   // host-driven loop: batches of 8 iterations, then read the done flag
   int done = 0;
   for (int it = 0; it < maxit + 4 && !done; it += 8) {
-    for (int k = 0; k < 8; ++k) launch_iteration(P, k & 1, P->stream, false);
-    CSL_TRY(cudaGetLastError());
+    for (int k = 0; k < 8; ++k) CSL_TRY(launch_iteration(P, k & 1, P->stream, false));
     CSL_TRY(cudaMemcpyAsync(&done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     CSL_TRY(cudaStreamSynchronize(P->stream));
   }
@@ -467,8 +434,7 @@ csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status
   DevState h;
   CSL_TRY(cudaMemcpyAsync(&h, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->stream));
   CSL_TRY(cudaStreamSynchronize(P->stream));
-  *solve_status = (csl_status)h.status;
-  if (!h.done) *solve_status = CSL_NOT_CONVERGED;
+  *solve_status = h.done ? (csl_status)h.status : CSL_NOT_CONVERGED;
   if (info) {
     memset(info, 0, sizeof(*info));
     info->iters = h.iter;
@@ -481,25 +447,15 @@ csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status
     const int per_iter = P->dim == 2 ? 4 : 6;
     const int prologue = 1 + per_iter;
     const int bodies = (h.loops + 1) / 2;
-    info->launches = prologue + (P->graph_state == 1 ? bodies * 2 * per_iter : h.loops * per_iter);
+    info->launches = prologue + (P->graph_state == 1 ? bodies * 2 * per_iter : ((h.loops + 7) / 8) * 8 * per_iter);
   }
   return CSL_OK;
 }
 
-csl_status solve_impl(csl_plan* P, const double* f, double* z, double tol, int maxit, csl_solve_info* info,
-                      double beta) {
-  if (!P || !f || !z) return CSL_INVALID_ARG;
+csl_status solve_impl(csl_plan* P, const double2* f, double tol, int maxit, double beta) {
   if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
-  launch_prologue(P, (const double2*)f, tol, maxit, beta, P->stream);
-  CSL_TRY(cudaGetLastError());
-  csl_status s = run_loop(P, maxit);
-  if (s != CSL_OK) return s;
-  CSL_TRY(cudaMemcpyAsync(z, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
-  CSL_TRY(cudaGetLastError());
-  csl_status st = CSL_OK;
-  s = read_info(P, info, &st);
-  if (s != CSL_OK) return s;
-  return st;
+  CSL_TRY(launch_prologue(P, f, tol, maxit, beta, P->stream));
+  return run_loop(P, maxit);
 }
 
 }  // namespace
@@ -509,7 +465,7 @@ csl_status solve_impl(csl_plan* P, const double* f, double* z, double tol, int m
 // ============================================================================
 extern "C" {
 
-const char* csl_version(void) { return "csl 0.1 (sm_103a)"; }
+const char* csl_version(void) { return "csl 0.2 (sm_103a)"; }
 
 const char* csl_last_error(void) { return g_last_error; }
 
@@ -546,7 +502,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   if (!isfinite(alpha) || !isfinite(beta)) return CSL_INVALID_ARG;
   for (int d = 0; d < dim; ++d) {
     if (!coef_faces[d] || n[d] < 1) return CSL_INVALID_ARG;
-    if (n[d] + 1 < 4 || n[d] + 1 > 2048 || ilog2_exact(n[d] + 1) < 0) return CSL_UNSUPPORTED_SIZE;
+    if (n[d] + 1 < 4 || n[d] + 1 > 1024 || ilog2_exact(n[d] + 1) < 0) return CSL_UNSUPPORTED_SIZE;
   }
   csl_plan_options o;
   csl_plan_options_init(&o);
@@ -577,31 +533,31 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   nface[2] = dim == 3 ? (long)(nz + 1) * ny * nx : 0;
 
   cudaError_t err = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
-  P->cx = (double*)dalloc<double>(P, nface[0] * 8, &err);
-  P->cy = (double*)dalloc<double>(P, nface[1] * 8, &err);
-  if (dim == 3) P->cz = (double*)dalloc<double>(P, nface[2] * 8, &err);
-  P->dg = (double*)dalloc<double>(P, M * 8, &err);
-  if (o.precision == CSL_PREC_FP64) P->stab = (double*)dalloc<double>(P, M * 8, &err);
+  P->cx = (double*)dalloc(P, nface[0] * 8, &err);
+  P->cy = (double*)dalloc(P, nface[1] * 8, &err);
+  if (dim == 3) P->cz = (double*)dalloc(P, nface[2] * 8, &err);
+  P->dg = (double*)dalloc(P, M * 8, &err);
+  if (o.precision == CSL_PREC_FP64) P->stab = (double*)dalloc(P, M * 8, &err);
   for (int d = 0; d < dim; ++d) {
     const int N = P->n[d] + 1;
-    P->mu_d[d] = (double*)dalloc<double>(P, (size_t)P->n[d] * 8, &err);
-    P->mu_f[d] = (float*)dalloc<float>(P, (size_t)P->n[d] * 4, &err);
-    P->tw[d] = dalloc<double>(P, (size_t)(N / 2) * 2 * tsz, &err);
-    P->hs[d] = dalloc<double>(P, (size_t)(N / 2 + 1) * tsz, &err);
+    P->mu_d[d] = (double*)dalloc(P, (size_t)P->n[d] * 8, &err);
+    P->mu_f[d] = (float*)dalloc(P, (size_t)P->n[d] * 4, &err);
+    P->tw[d] = dalloc(P, (size_t)(N / 2) * 2 * tsz, &err);
+    P->hs[d] = dalloc(P, (size_t)(N / 2 + 1) * tsz, &err);
   }
-  P->b = (double2*)dalloc<double>(P, M * 16, &err);
-  P->x = (double2*)dalloc<double>(P, M * 16, &err);
-  P->io = (double2*)dalloc<double>(P, M * 16, &err);
+  P->b = (double2*)dalloc(P, M * 16, &err);
+  P->x = (double2*)dalloc(P, M * 16, &err);
+  P->io = (double2*)dalloc(P, M * 16, &err);
   for (int i = 0; i < 2; ++i) {
-    P->v[i] = (double2*)dalloc<double>(P, M * 16, &err);
-    P->w[i] = (double2*)dalloc<double>(P, M * 16, &err);
-    P->z[i] = dalloc<double>(P, M * 2 * tsz, &err);
+    P->v[i] = (double2*)dalloc(P, M * 16, &err);
+    P->w[i] = (double2*)dalloc(P, M * 16, &err);
+    P->z[i] = dalloc(P, M * 2 * tsz, &err);
   }
-  P->T = dalloc<double>(P, M * 2 * tsz, &err);
-  P->st = (DevState*)dalloc<double>(P, sizeof(DevState), &err);
-  P->st_prof = (DevState*)dalloc<double>(P, sizeof(DevState), &err);
-  P->partials = (double*)dalloc<double>(P, (size_t)kMaxRedBlocks * 4 * 8, &err);
-  P->u64 = (unsigned long long*)dalloc<double>(P, 8 * 8, &err);
+  P->T = dalloc(P, M * 2 * tsz, &err);
+  P->st = (DevState*)dalloc(P, sizeof(DevState), &err);
+  P->st_prof = (DevState*)dalloc(P, sizeof(DevState), &err);
+  P->partials = (double*)dalloc(P, (size_t)kMaxRedBlocks * 4 * 8, &err);
+  P->u64 = (unsigned long long*)dalloc(P, 8 * 8, &err);
   if (err != cudaSuccess) {
     CSL_NOTE(err, "device allocation");
     (void)cudaGetLastError();
@@ -610,7 +566,11 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   cudaStream_t s = P->stream;
   P->ew_blocks = (int)((M + 255) / 256 < kSMs * 8 ? (M + 255) / 256 : kSMs * 8);
-  P->sten_blocks = P->ew_blocks;
+  {
+    const long strips = stencil_strips(dim, nx, ny, nz);  // one warp per strip, 8 warps per CTA
+    const long blocks = (strips + 7) / 8;
+    P->sten_blocks = (int)(blocks < kSMs * 8 ? blocks : kSMs * 8);
+  }
 
   // coefficient faces: a_e / h^2, min / max / validity (Eq. 1 and Eq. 4's a_min, a_max)
   {
@@ -621,7 +581,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       err = cudaMemcpyAsync(P->u64, init, sizeof(init), cudaMemcpyHostToDevice, s);
       if (err == cudaSuccess) {
         const long cnt = nface[d];
-        int blocks = (int)((cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024);
+        const int blocks = (int)((cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024);
         k_scale_faces<<<blocks, 256, 0, s>>>(coef_faces[d], dst[d], cnt, 1.0 / (P->h[d] * P->h[d]), P->u64);
         err = cudaGetLastError();
       }
@@ -660,7 +620,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
 
   // Section 2.3 tables: 1D Laplacian eigenvalues, FFT twiddles, half sines
   P->cnorm = 1.0;
-  for (int d = 0; d < dim; ++d) {
+  for (int d = 0; d < dim && err == cudaSuccess; ++d) {
     const int nd = P->n[d], N = nd + 1;
     P->cnorm *= 2.0 / (double)N;
     std::vector<double> mu(nd);
@@ -677,7 +637,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     }
     for (int j = 0; j <= N / 2; ++j) hsd[j] = 0.5 * sin(M_PI * (double)j / N);
     hsd[N / 2] = 0.5;
-    if (err == cudaSuccess) err = cudaMemcpy(P->mu_d[d], mu.data(), nd * 8, cudaMemcpyHostToDevice);
+    err = cudaMemcpy(P->mu_d[d], mu.data(), nd * 8, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(P->mu_f[d], muf.data(), nd * 4, cudaMemcpyHostToDevice);
     if (o.precision == CSL_PREC_FP32) {
       std::vector<float> twf(N), hsf(N / 2 + 1);
@@ -726,8 +686,9 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     return CSL_CUDA_ERROR;
   }
   // launch configurations of the sine-transform passes
+  const long nrows = M / nx;
   if (o.precision == CSL_PREC_FP32) {
-    config_row<float>(P->row, nx, (int)(M / nx));
+    config_row<float>(P->row, nx, (int)nrows);
     if (dim == 2) {
       config_strided<float>(P->sy, ny, nx, 1, 0, nx, o.lines_per_cta);
     } else {
@@ -735,7 +696,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       config_strided<float>(P->sz, nz, nx, ny, nx, (long)nx * ny, o.lines_per_cta);
     }
   } else {
-    config_row<double>(P->row, nx, (int)(M / nx));
+    config_row<double>(P->row, nx, (int)nrows);
     if (dim == 2) {
       config_strided<double>(P->sy, ny, nx, 1, 0, nx, o.lines_per_cta);
     } else {
@@ -783,21 +744,30 @@ csl_status csl_apply(csl_plan* P, const double* z, double* out) {
 csl_status csl_precondition(csl_plan* P, const double* v, double* out) {
   if (!P || !v || !out) return CSL_INVALID_ARG;
   if (P->precision == CSL_PREC_FP32)
-    launch_precondition_T<float>(P, (const double2*)v, (double2*)out, P->stream);
+    CSL_TRY(launch_precondition_T<float>(P, (const double2*)v, (double2*)out, P->stream));
   else
-    launch_precondition_T<double>(P, (const double2*)v, (double2*)out, P->stream);
-  CSL_TRY(cudaGetLastError());
+    CSL_TRY(launch_precondition_T<double>(P, (const double2*)v, (double2*)out, P->stream));
   return CSL_OK;
 }
 
-csl_status csl_solve(csl_plan* plan, const double* f, double* z, double tol, int maxit, csl_solve_info* info) {
-  if (!plan) return CSL_INVALID_ARG;
-  return solve_impl(plan, f, z, tol, maxit, info, plan->beta);
+csl_status csl_solve(csl_plan* P, const double* f, double* z, double tol, int maxit, csl_solve_info* info) {
+  if (!P || !f || !z) return CSL_INVALID_ARG;
+  csl_status s = solve_impl(P, (const double2*)f, tol, maxit, P->beta);
+  if (s != CSL_OK) return s;
+  CSL_TRY(cudaMemcpyAsync(z, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  csl_status st = CSL_OK;
+  s = read_info(P, info, &st);
+  return s != CSL_OK ? s : st;
 }
 
-csl_status csl_adjoint(csl_plan* plan, const double* g, double* y, double tol, int maxit, csl_solve_info* info) {
-  if (!plan) return CSL_INVALID_ARG;
-  return solve_impl(plan, g, y, tol, maxit, info, -plan->beta);
+csl_status csl_adjoint(csl_plan* P, const double* g, double* y, double tol, int maxit, csl_solve_info* info) {
+  if (!P || !g || !y) return CSL_INVALID_ARG;
+  csl_status s = solve_impl(P, (const double2*)g, tol, maxit, -P->beta);
+  if (s != CSL_OK) return s;
+  CSL_TRY(cudaMemcpyAsync(y, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  csl_status st = CSL_OK;
+  s = read_info(P, info, &st);
+  return s != CSL_OK ? s : st;
 }
 
 csl_status csl_solve_host(csl_plan* P, const double* f_host, double* z_host, double tol, int maxit,
@@ -806,15 +776,12 @@ csl_status csl_solve_host(csl_plan* P, const double* f_host, double* z_host, dou
   if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
   const size_t bytes = sizeof(double2) * P->M;
   CSL_TRY(cudaMemcpyAsync(P->io, f_host, bytes, cudaMemcpyHostToDevice, P->stream));
-  launch_prologue(P, P->io, tol, maxit, P->beta, P->stream);
-  CSL_TRY(cudaGetLastError());
-  csl_status s = run_loop(P, maxit);
+  csl_status s = solve_impl(P, P->io, tol, maxit, P->beta);
   if (s != CSL_OK) return s;
   CSL_TRY(cudaMemcpyAsync(z_host, P->x, bytes, cudaMemcpyDeviceToHost, P->stream));
   csl_status st = CSL_OK;
   s = read_info(P, info, &st);
-  if (s != CSL_OK) return s;
-  return st;
+  return s != CSL_OK ? s : st;
 }
 
 csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* const grad_faces[3]) {
@@ -847,80 +814,55 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   h.tol = 1e-300;
   h.maxit = 1 << 30;
   h.beta = P->beta;
-  h.sqrt_pmin = h.sqrt_pmax = 0.0;
   DevState* keep = P->st;
   P->st = P->st_prof;  // all launches below read the scratch state
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   const bool fp32 = P->precision == CSL_PREC_FP32;
-  int k = 0;
   const int nk = P->dim == 2 ? 4 : 6;
   static const char* n2[4] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
                               "k_row<LOAD_T,STORE_Z_UPDATE>"};
   static const char* n3[6] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
                               "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>"};
+  int k = 0;
   for (k = 0; k < nk && err == cudaSuccess; ++k) {
     double tot = 0.0;
     for (int r = 0; r < reps && err == cudaSuccess; ++r) {
       err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
-      if (err != cudaSuccess) break;
-      err = cudaEventRecord(e0, P->stream);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, P->stream);
       if (err != cudaSuccess) break;
       const int par = r & 1;
-      const bool last = (k == nk - 1);
       if (k == 0) {
-        if (fp32) launch_stencil<float>(P, par, P->stream, false);
-        else launch_stencil<double>(P, par, P->stream, false);
+        err = fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
       } else if (k == 1) {
-        if (fp32) {
-          RowArgs<float> a = row_args<float>(P);
-          a.vnew = P->v[1 - par]; a.vcur = P->v[par]; a.tout = (float2*)P->T; a.st = P->st;
-          launch_row<float, LOAD_LANCZOS, STORE_T>(P, a, P->stream);
-        } else {
-          RowArgs<double> a = row_args<double>(P);
-          a.vnew = P->v[1 - par]; a.vcur = P->v[par]; a.tout = (double2*)P->T; a.st = P->st;
-          launch_row<double, LOAD_LANCZOS, STORE_T>(P, a, P->stream);
-        }
-      } else if (last) {
-        if (fp32) {
-          RowArgs<float> a = row_args<float>(P);
-          a.tin = (const float2*)P->T; a.zout = (float2*)P->z[1 - par]; a.zcur = (const float2*)P->z[par];
-          a.wprev = P->w[par]; a.wcur = P->w[1 - par]; a.x = P->x; a.st = P->st;
-          launch_row<float, LOAD_T, STORE_Z_UPDATE>(P, a, P->stream);
-        } else {
-          RowArgs<double> a = row_args<double>(P);
-          a.tin = (const double2*)P->T; a.zout = (double2*)P->z[1 - par]; a.zcur = (const double2*)P->z[par];
-          a.wprev = P->w[par]; a.wcur = P->w[1 - par]; a.x = P->x; a.st = P->st;
-          launch_row<double, LOAD_T, STORE_Z_UPDATE>(P, a, P->stream);
-        }
+        err = fp32 ? run_row<float>(P, LOAD_LANCZOS, STORE_T, p1_args<float>(P, par), P->stream)
+                   : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
+      } else if (k == nk - 1) {
+        err = fp32 ? run_row<float>(P, LOAD_T, STORE_Z_UPDATE, p3_args<float>(P, par), P->stream)
+                   : run_row<double>(P, LOAD_T, STORE_Z_UPDATE, p3_args<double>(P, par), P->stream);
       } else {
         const bool mid = (P->dim == 2) || (k == 3);
-        const PassCfg& c = (P->dim == 2 || k != 3) ? P->sy : P->sz;
-        const int axis = (P->dim == 2 || k != 3) ? 1 : 2;
+        const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
+        const int axis = (P->dim == 3 && k == 3) ? 2 : 1;
         if (fp32) {
           StridedArgs<float> a = strided_args<float>(P, c, axis);
           a.st = P->st;
           if (mid) {
             fill_mid<float>(P, a, axis);
             a.scalar_mode = 2;
-            k_strided<float, true><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
-          } else {
-            k_strided<float, false><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
           }
+          err = launch_strided<float>(c.N, mid, a, c.L, P->stream);
         } else {
           StridedArgs<double> a = strided_args<double>(P, c, axis);
           a.st = P->st;
           if (mid) {
             fill_mid<double>(P, a, axis);
             a.scalar_mode = 2;
-            k_strided<double, true><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
-          } else {
-            k_strided<double, false><<<c.blocks, c.threads, c.smem, P->stream>>>(a);
           }
+          err = launch_strided<double>(c.N, mid, a, c.L, P->stream);
         }
       }
-      err = cudaGetLastError();
       if (err == cudaSuccess) err = cudaEventRecord(e1, P->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float t = 0.f;

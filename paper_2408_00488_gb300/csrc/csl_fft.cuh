@@ -1,0 +1,269 @@
+// Sine transform DST-I of length n = N - 1 (N = 2^k <= 1024) on one line held
+// in shared memory, computed by the TPL lanes of one warp (Section 2.3:
+// W_{jk} = sqrt(2/N) sin(pi j k/N) is real, symmetric and orthogonal, so the
+// unnormalised S_{jk} = sin(pi j k/N) serves forward and inverse; the factor
+// 2/N per axis and pair of transforms is folded into the per-mode scale).
+//
+// One complex line carries both real blocks of the 2x2 system (real part =
+// block 1, imaginary part = block 2); S is real, so S(x + i y) = Sx + i Sy.
+//
+// Algorithm: one length-N complex FFT per line.
+//   y_j = s_j (z_j + z_{N-j})/2 + (z_j - z_{N-j})/4,  s_j = sin(pi j/N), z_0 = z_N = 0
+//   Y = FFT_N(y)   (exp(-2 pi i jk/N))
+//   C_k = Y_k + Y_{N-k},  S_k = i (Y_k - Y_{N-k})
+//   (S z)_{2k}   = S_k                      k = 1 .. N/2-1
+//   (S z)_{2k+1} = Y_0 + C_1 + ... + C_k    k = 0 .. N/2-1   (prefix sum)
+// (2 sin a cos b = sin(a+b) - sin(b-a) applied to the cosine and sine sums of y.)
+//
+// The FFT is a four-step transform N = R1 * R2: lane g computes a radix-R1
+// DFT over the samples j = g + R2 r held in registers, multiplies by
+// w_N^{g k1} and writes them to shared memory; lanes then take radix-R2 DFTs
+// over g.  Each radix-R DFT is unrolled in registers (radix-2 stages with the
+// trivial twiddles 1 and -i removed at compile time).  All lanes of a line sit
+// in one warp, so only __syncwarp() orders the shared-memory exchanges.
+//
+// The result is left in the line buffer in a padded order: element m at
+// out_pos(m) (odd m in a scan layout with one pad slot per chunk, even m in a
+// separate region), so that the prefix scan and the split are free of bank
+// conflicts.
+#pragma once
+#include "csl_common.cuh"
+
+namespace csl {
+
+template <int N> struct DstShape;
+template <> struct DstShape<4> { enum { R1 = 4, R2 = 1, TPL = 1 }; };
+template <> struct DstShape<8> { enum { R1 = 8, R2 = 1, TPL = 1 }; };
+template <> struct DstShape<16> { enum { R1 = 16, R2 = 1, TPL = 1 }; };
+template <> struct DstShape<32> { enum { R1 = 32, R2 = 1, TPL = 1 }; };
+template <> struct DstShape<64> { enum { R1 = 8, R2 = 8, TPL = 8 }; };
+template <> struct DstShape<128> { enum { R1 = 16, R2 = 8, TPL = 8 }; };
+template <> struct DstShape<256> { enum { R1 = 16, R2 = 16, TPL = 16 }; };
+template <> struct DstShape<512> { enum { R1 = 32, R2 = 16, TPL = 16 }; };
+template <> struct DstShape<1024> { enum { R1 = 32, R2 = 32, TPL = 32 }; };
+
+// shared-memory line stride (complex elements); odd, so that column-wise tile
+// loads (consecutive threads -> consecutive lines) hit distinct banks
+template <int N>
+__host__ __device__ constexpr int dst_line_stride() {
+  return N + DstShape<N>::R2 + 1;
+}
+
+template <int N>
+__device__ __forceinline__ int dst_out_pos(int m) {
+  constexpr int H = N / 2, TPL = DstShape<N>::TPL, CH = H / TPL;
+  constexpr int SBASE = H + TPL - 1;
+  if (m & 1) {
+    const int k = m >> 1;
+    return k + k / CH;
+  }
+  return SBASE + (m >> 1) - 1;
+}
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t cmul(typename C2<T>::t a, typename C2<T>::t b) {
+  return mkc<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t cadd(typename C2<T>::t a, typename C2<T>::t b) {
+  return mkc<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t csub(typename C2<T>::t a, typename C2<T>::t b) {
+  return mkc<T>(a.x - b.x, a.y - b.y);
+}
+
+template <int R>
+__host__ __device__ constexpr int bit_reverse(int i) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// w_N^m for 0 <= m < N from the half table tw[m] = exp(-2 pi i m/N), m < N/2
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t tw_full(const typename C2<T>::t* tw, int m, int H) {
+  if (m < H) return tw[m];
+  const typename C2<T>::t v = tw[m - H];
+  return mkc<T>(-v.x, -v.y);
+}
+
+// In-register forward DFT of length R (natural order in and out).  The table
+// holds w_N^m, and w_R^k = w_N^{k * TWS} with TWS = N/R.
+template <typename T, int R, int TWS>
+__device__ __forceinline__ void dft_reg(typename C2<T>::t (&x)[R], const typename C2<T>::t* tw) {
+  typedef typename C2<T>::t c_t;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = bit_reverse<R>(i);
+    if (j > i) {
+      const c_t t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int s = 1; s < R; s <<= 1) {
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      c_t w = mkc<T>((T)1, (T)0);
+      if (k != 0 && 2 * k != s) w = tw[k * (R / (2 * s)) * TWS];  // w_{2s}^k
+#pragma unroll
+      for (int b = 0; b < R; b += 2 * s) {
+        const c_t u = x[b + k], v = x[b + k + s];
+        c_t t;
+        if (k == 0)
+          t = v;
+        else if (2 * k == s)
+          t = mkc<T>(v.y, -v.x);  // times -i
+        else
+          t = cmul<T>(w, v);
+        x[b + k] = cadd<T>(u, t);
+        x[b + k + s] = csub<T>(u, t);
+      }
+    }
+  }
+}
+
+// y_j of the pre-twiddle, from the line input (natural or out_pos order)
+template <typename T, int N, bool PERM_IN>
+__device__ __forceinline__ typename C2<T>::t pre_twiddle(const typename C2<T>::t* a, const T* hs, int j) {
+  typedef typename C2<T>::t c_t;
+  if (j == 0) return mkc<T>((T)0, (T)0);
+  const int jm = N - j;
+  const c_t zj = a[PERM_IN ? dst_out_pos<N>(j) : j];
+  const c_t zm = a[PERM_IN ? dst_out_pos<N>(jm) : jm];
+  const T h = hs[j < jm ? j : jm];
+  const T dx = (zj.x - zm.x) * (T)0.25, dy = (zj.y - zm.y) * (T)0.25;
+  return mkc<T>(fma(h, zj.x + zm.x, dx), fma(h, zj.y + zm.y, dy));
+}
+
+// Unnormalised DST-I of one line in place: input at natural positions 1..N-1
+// (or at out_pos when PERM_IN), output at out_pos.  Called by all TPL lanes of
+// the line (lane index t); every lane of the warp must call it.
+template <typename T, int N, bool PERM_IN>
+__device__ __forceinline__ void dst_line(typename C2<T>::t* a, int t, const typename C2<T>::t* tw,
+                                         const T* hs) {
+  typedef typename C2<T>::t c_t;
+  typedef DstShape<N> S;
+  constexpr int R1 = S::R1, R2 = S::R2, TPL = S::TPL, H = N / 2, CH = H / TPL;
+  constexpr int SBASE = H + TPL - 1;
+  if (R2 == 1) {
+    // whole line in one thread
+    c_t x[R1];
+#pragma unroll
+    for (int j = 0; j < R1; ++j) x[j] = pre_twiddle<T, N, PERM_IN>(a, hs, j);
+    dft_reg<T, R1, N / R1>(x, tw);
+    c_t run = x[0];
+    a[0] = run;  // (S z)_1
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+      const c_t Yk = x[k], Ym = x[N - k];
+      run = cadd<T>(run, cadd<T>(Yk, Ym));
+      a[k] = run;                                               // (S z)_{2k+1} at k
+      a[SBASE + k - 1] = mkc<T>(Ym.y - Yk.y, Yk.x - Ym.x);   // (S z)_{2k}
+    }
+    return;
+  }
+  // ---- pass 1: lane g, radix-R1 DFT over j = g + R2 r, twiddle w_N^{g k1}
+  {
+    const int g = t;
+    c_t x[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) x[r] = pre_twiddle<T, N, PERM_IN>(a, hs, g + R2 * r);
+    dft_reg<T, R1, N / R1>(x, tw);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) x[k1] = cmul<T>(x[k1], tw_full<T>(tw, g * k1, H));
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[g * (R1 + 1) + k1] = x[k1];
+    __syncwarp();
+  }
+  // ---- pass 2: lane takes k1 = t + TPL i, radix-R2 DFT over g
+  {
+    constexpr int NG = R1 / TPL;
+    c_t x[NG][R2];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      const int k1 = t + TPL * i;
+#pragma unroll
+      for (int g = 0; g < R2; ++g) x[i][g] = a[g * (R1 + 1) + k1];
+      dft_reg<T, R2, N / R2>(x[i], tw);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      const int k1 = t + TPL * i;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = x[i][k2];  // Y natural order
+    }
+    __syncwarp();
+  }
+  // ---- split into C_k (scan layout) and S_k
+  {
+    c_t cc[CH], ss[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int k = t + TPL * i;
+      const c_t Yk = a[k];
+      if (k == 0) {
+        cc[i] = Yk;
+        ss[i] = Yk;
+      } else {
+        const c_t Ym = a[N - k];
+        cc[i] = cadd<T>(Yk, Ym);
+        ss[i] = mkc<T>(Ym.y - Yk.y, Yk.x - Ym.x);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int k = t + TPL * i;
+      a[k + k / CH] = cc[i];
+      if (k != 0) a[SBASE + k - 1] = ss[i];
+    }
+    __syncwarp();
+  }
+  // ---- prefix sum of C over k (chunk of CH per lane, segmented warp scan)
+  {
+    c_t* c = a + t * (CH + 1);
+    c_t v[CH];
+    c_t sum = mkc<T>((T)0, (T)0);
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      v[i] = c[i];
+      sum = cadd<T>(sum, v[i]);
+    }
+    c_t inc = sum;
+#pragma unroll
+    for (int d = 1; d < TPL; d <<= 1) {
+      const T ux = __shfl_up_sync(0xffffffffu, inc.x, d, TPL);
+      const T uy = __shfl_up_sync(0xffffffffu, inc.y, d, TPL);
+      if (t >= d) {
+        inc.x += ux;
+        inc.y += uy;
+      }
+    }
+    c_t run = csub<T>(inc, sum);
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      run = cadd<T>(run, v[i]);
+      c[i] = run;
+    }
+    __syncwarp();
+  }
+}
+
+// Copy the transform tables of length N into shared memory (block-wide).
+template <typename T>
+__device__ __forceinline__ void load_tables(typename C2<T>::t* s_tw, T* s_hs, const typename C2<T>::t* g_tw,
+                                            const T* g_hs, int N) {
+  const int H = N >> 1;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) s_tw[i] = g_tw[i];
+  for (int i = threadIdx.x; i <= H; i += blockDim.x) s_hs[i] = g_hs[i];
+}
+
+}  // namespace csl

@@ -18,7 +18,6 @@
 // last block to finish), so repeated solves are bitwise identical.
 #pragma once
 #include "csl_common.cuh"
-#include "csl_dst.cuh"
 
 namespace csl {
 
@@ -110,6 +109,90 @@ struct StencilArgs {
   int use_cond;
 };
 
+// Rows (2D) or planes (3D) one warp walks per strip of the stencil kernel.
+constexpr int kStencilStrip = 16;
+
+__device__ __forceinline__ double2 shfl_up_d2(double2 v) {
+  return make_double2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ double2 shfl_down_d2(double2 v) {
+  return make_double2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// Number of warp strips of k_stencil (32 x-columns by kStencilStrip steps
+// along the marching axis: y in 2D, z in 3D).
+__host__ __device__ inline long stencil_strips(int dim, int nx, int ny, int nz) {
+  const long nsx = (nx + 31) / 32;
+  const long nm = dim == 2 ? ny : nz;
+  return nsx * ((nm + kStencilStrip - 1) / kStencilStrip) * (dim == 3 ? ny : 1);
+}
+
+// One value of a strip and its marching window: m-1, m, m+1 along the strip,
+// x-1 / x+1 by warp shuffles (the strip's edge lanes load theirs), and in 3D
+// y-1 / y+1 by direct loads.  Every value is converted to FP64 once.
+template <int DIM, typename TZ>
+struct StripWindow {
+  double2 zm, zc, zp;
+  __device__ __forceinline__ void start(const TZ* z, long base, long mstride, int m0, bool vx) {
+    const double2 zero = make_double2(0.0, 0.0);
+    zm = (vx && m0 > 0) ? to_d2(z[base + (long)(m0 - 1) * mstride]) : zero;
+    zc = vx ? to_d2(z[base + (long)m0 * mstride]) : zero;
+  }
+  // (K + alpha I) applied at the current point; call with all 32 lanes
+  __device__ __forceinline__ double2 KA(const TZ* z, const StencilArgs& a, long p, long mstride, int m, int nm,
+                                        int x, int yfix, bool vx, int lane) {
+    const double2 zero = make_double2(0.0, 0.0);
+    const int nx = a.g.nx, ny = a.g.ny;
+    zp = (vx && m + 1 < nm) ? to_d2(z[p + mstride]) : zero;
+    double2 zl = shfl_up_d2(zc), zr = shfl_down_d2(zc);
+    if (lane == 0) zl = (vx && x > 0) ? to_d2(z[p - 1]) : zero;
+    if (lane == 31) zr = (x + 1 < nx) ? to_d2(z[p + 1]) : zero;
+    double2 t = zero;
+    if (vx) {
+      const double d = a.dg[p];
+      double ax = d * zc.x, ay = d * zc.y;
+      long rx, ry;
+      if (DIM == 2) {
+        rx = (long)m * (nx + 1) + x;
+        ry = (long)m * nx + x;
+      } else {
+        rx = ((long)m * ny + yfix) * (nx + 1) + x;
+        ry = ((long)m * (ny + 1) + yfix) * nx + x;
+      }
+      const double cw = a.cx[rx], ce = a.cx[rx + 1];
+      ax = fma(-cw, zl.x, ax);
+      ay = fma(-cw, zl.y, ay);
+      ax = fma(-ce, zr.x, ax);
+      ay = fma(-ce, zr.y, ay);
+      const double cs = a.cy[ry], cn = a.cy[ry + nx];
+      if (DIM == 2) {  // y is the marching axis
+        ax = fma(-cs, zm.x, ax);
+        ay = fma(-cs, zm.y, ay);
+        ax = fma(-cn, zp.x, ax);
+        ay = fma(-cn, zp.y, ay);
+      } else {
+        const double2 zs = yfix > 0 ? to_d2(z[p - nx]) : zero;
+        const double2 zn = yfix < ny - 1 ? to_d2(z[p + nx]) : zero;
+        ax = fma(-cs, zs.x, ax);
+        ay = fma(-cs, zs.y, ay);
+        ax = fma(-cn, zn.x, ax);
+        ay = fma(-cn, zn.y, ay);
+        const double cd = a.cz[p], cu = a.cz[p + mstride];  // z-faces share the point's index
+        ax = fma(-cd, zm.x, ax);
+        ay = fma(-cd, zm.y, ay);
+        ax = fma(-cu, zp.x, ax);
+        ay = fma(-cu, zp.y, ay);
+      }
+      t = make_double2(ax, ay);
+    }
+    return t;
+  }
+  __device__ __forceinline__ void advance() {
+    zm = zc;
+    zc = zp;
+  }
+};
+
 template <int DIM, typename TZ>
 __global__ void __launch_bounds__(256) k_stencil(StencilArgs a) {
   DevState* st = a.st;
@@ -122,23 +205,46 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a) {
   const double inv_g = 1.0 / gam, lanc = gam / gam_old;
   const int check = st->check;
   const TZ* z = (const TZ*)a.z;
+  const int nx = a.g.nx, ny = a.g.ny;
+  const int nm = DIM == 2 ? a.g.ny : a.g.nz;
+  const long mstride = DIM == 2 ? (long)nx : (long)nx * ny;
+  const int lane = threadIdx.x & 31;
+  const long nsx = (nx + 31) / 32, nsm = (nm + kStencilStrip - 1) / kStencilStrip;
+  const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz);
   double acc[2] = {0.0, 0.0};
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < a.g.M; p += (long)gridDim.x * blockDim.x) {
-    int ix, iy, iz;
-    point_coords(p, a.g, ix, iy, iz);
-    double2 zc;
-    const double2 t = stencil_KA<DIM, TZ>(z, a.cx, a.cy, a.cz, a.dg, a.g, p, ix, iy, iz, zc);
-    const double2 Az = block_A(t, zc, beta);
-    acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
-    const double2 vo = a.vold[p];
-    a.vold[p] = make_double2(fma(Az.x, inv_g, -lanc * vo.x), fma(Az.y, inv_g, -lanc * vo.y));
-    if (check) {
-      double2 xc;
-      const double2 tx = stencil_KA<DIM, double2>(a.x, a.cx, a.cy, a.cz, a.dg, a.g, p, ix, iy, iz, xc);
-      const double2 Ax = block_A(tx, xc, beta);
-      const double2 bb = a.b[p];
-      const double rx = bb.x - Ax.x, ry = bb.y - Ax.y;
-      acc[1] = fma(rx, rx, fma(ry, ry, acc[1]));
+  for (long s = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
+       s += (long)gridDim.x * (blockDim.x >> 5)) {
+    const int sx = (int)(s % nsx);
+    const int sm = (int)((s / nsx) % nsm);
+    const int yfix = DIM == 3 ? (int)(s / (nsx * nsm)) : 0;
+    const int x = sx * 32 + lane;
+    const bool vx = x < nx;
+    const int m0 = sm * kStencilStrip, m1 = min(m0 + kStencilStrip, nm);
+    const long base = DIM == 2 ? (long)x : (long)yfix * nx + x;
+    StripWindow<DIM, TZ> wz;
+    StripWindow<DIM, double2> wx;
+    wz.start(z, base, mstride, m0, vx);
+    if (check) wx.start(a.x, base, mstride, m0, vx);
+    for (int m = m0; m < m1; ++m) {
+      const long p = base + (long)m * mstride;
+      const double2 t = wz.KA(z, a, p, mstride, m, nm, x, yfix, vx, lane);
+      double2 tx = make_double2(0.0, 0.0);
+      if (check) tx = wx.KA(a.x, a, p, mstride, m, nm, x, yfix, vx, lane);
+      if (vx) {
+        const double2 zc = wz.zc;
+        const double2 Az = block_A(t, zc, beta);
+        acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
+        const double2 vo = a.vold[p];
+        a.vold[p] = make_double2(fma(Az.x, inv_g, -lanc * vo.x), fma(Az.y, inv_g, -lanc * vo.y));
+        if (check) {
+          const double2 Ax = block_A(tx, wx.zc, beta);
+          const double2 bb = a.b[p];
+          const double rx = bb.x - Ax.x, ry = bb.y - Ax.y;
+          acc[1] = fma(rx, rx, fma(ry, ry, acc[1]));
+        }
+      }
+      wz.advance();
+      if (check) wx.advance();
     }
   }
   double tot[2];
@@ -195,7 +301,7 @@ __global__ void __launch_bounds__(256) k_apply(Grid g, const double2* z, double2
 // of w and x, and decide whether the next stencil pass evaluates the true
 // residual.
 // ---------------------------------------------------------------------------
-__device__ void givens_step(DevState* st, double g2) {
+__device__ inline void givens_step(DevState* st, double g2) {
   if (!(g2 >= 0.0) || !(g2 < 1e300)) {
     st->done = 1;
     st->status = ST_BREAKDOWN;
@@ -246,232 +352,6 @@ __device__ void givens_step(DevState* st, double g2) {
 }
 
 // ---------------------------------------------------------------------------
-// Row pass: DST along x for rows of n_x contiguous points.
-// ---------------------------------------------------------------------------
-enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2 };
-enum { STORE_T = 0, STORE_D = 1, STORE_Z = 2, STORE_Z_UPDATE = 3 };
-
-template <typename T>
-struct RowArgs {
-  int logn, n, nrows;   // line length n = N - 1
-  int G, TL, LS;        // lines per CTA, threads per line, smem line stride
-  const typename C2<T>::t* tw;
-  const T* hs;
-  const double2* vin;             // LOAD_V
-  const typename C2<T>::t* tin;   // LOAD_T
-  double2* vnew;                  // LOAD_LANCZOS: u' in, v_{j+1} out
-  const double2* vcur;            // LOAD_LANCZOS: v_j
-  typename C2<T>::t* tout;        // STORE_T
-  double2* dout;                  // STORE_D
-  typename C2<T>::t* zout;        // STORE_Z*: z_{j+1}
-  const typename C2<T>::t* zcur;  // STORE_Z_UPDATE: z_j
-  double2* wprev;                 // in w_{j-1}, out w_{j+1}
-  const double2* wcur;            // w_j
-  double2* x;
-  DevState* st;                   // may be null (precondition only)
-};
-
-template <typename T>
-__host__ __device__ inline size_t dst_smem_bytes(int lines, int LS, int logn, int TL) {
-  // two line buffers + twiddles + half-sines + scan scratch
-  const size_t H = (size_t)1 << (logn - 1);
-  const int nl = lines;
-  return (size_t)2 * nl * LS * sizeof(typename C2<T>::t) + H * sizeof(typename C2<T>::t) +
-         (H + 2) * sizeof(T) + (size_t)nl * 32 * sizeof(typename C2<T>::t) + 64;
-}
-
-template <typename T, int LOAD, int STORE>
-__global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
-  typedef typename C2<T>::t c_t;
-  if (a.st && a.st->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = 1 << a.logn, H = N >> 1;
-  c_t* A = (c_t*)smem_raw;
-  c_t* B = A + (size_t)a.G * a.LS;
-  c_t* s_tw = B + (size_t)a.G * a.LS;
-  c_t* s_scr = s_tw + H;
-  T* s_hs = (T*)(s_scr + (size_t)a.G * 32);
-  load_tables<T>(s_tw, s_hs, a.tw, a.hs, a.logn);
-  double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
-  if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
-  if (STORE == STORE_Z_UPDATE) {
-    wa = a.st->w_a;
-    wb = a.st->w_b;
-    wc = a.st->w_c;
-    xc = a.st->x_coef;
-  }
-  const int l = threadIdx.x / a.TL, t = threadIdx.x - l * a.TL;
-  const int n = a.n;
-  for (int row0 = blockIdx.x * a.G; row0 < a.nrows; row0 += gridDim.x * a.G) {
-    const int Gh = min(a.G, a.nrows - row0);
-    __syncthreads();  // tables ready / previous tile's buffers free
-    if (l < Gh) {
-      const long base = (long)(row0 + l) * n;
-      c_t* al = A + (size_t)l * a.LS;
-      for (int j = t; j < n; j += a.TL) {
-        const long p = base + j;
-        c_t val;
-        if (LOAD == LOAD_V) {
-          val = from_d2<T>(a.vin[p]);
-        } else if (LOAD == LOAD_T) {
-          val = a.tin[p];
-        } else {
-          const double2 u = a.vnew[p], vc = a.vcur[p];
-          const double2 vn = make_double2(fma(-lz, vc.x, u.x), fma(-lz, vc.y, u.y));
-          a.vnew[p] = vn;
-          val = from_d2<T>(vn);
-        }
-        al[j + 1] = val;
-      }
-    }
-    __syncthreads();
-    dst_lines<T, false>(A, B, a.LS, Gh, a.TL, a.logn, s_tw, s_hs, s_scr);
-    if (l < Gh) {
-      const long base = (long)(row0 + l) * n;
-      const c_t* al = A + (size_t)l * a.LS;
-      for (int j = t; j < n; j += a.TL) {
-        const long p = base + j;
-        const c_t F = al[dst_out_pos(j + 1, N)];
-        if (STORE == STORE_T) {
-          a.tout[p] = F;
-        } else if (STORE == STORE_D) {
-          a.dout[p] = to_d2(F);
-        } else {
-          a.zout[p] = F;
-          if (STORE == STORE_Z_UPDATE) {
-            const double2 zo = to_d2(a.zcur[p]);
-            const double2 wp = a.wprev[p], wq = a.wcur[p];
-            const double2 wn = make_double2(fma(wa, zo.x, fma(wb, wp.x, wc * wq.x)),
-                                            fma(wa, zo.y, fma(wb, wp.y, wc * wq.y)));
-            a.wprev[p] = wn;
-            const double2 xo = a.x[p];
-            a.x[p] = make_double2(fma(xc, wn.x, xo.x), fma(xc, wn.y, xo.y));
-          }
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Strided pass: DST along y or z (lines of stride line_stride), C adjacent
-// x-columns per tile, in place.  With MID: forward DST, per-mode scale of
-// P^{-1} (Eq. 4: s_k = cnorm / sqrt((gamma mu_k + alpha)^2 + beta^2)),
-// gamma^2 partial sums, inverse DST; then the scalar step.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
-__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
-
-template <typename T>
-struct StridedArgs {
-  int logn, n;            // line length n = N - 1
-  int ncols, nouter;      // x extent; number of outer blocks
-  long outer_stride, line_stride;
-  int C, TL, LS;
-  const typename C2<T>::t* tw;
-  const T* hs;
-  typename C2<T>::t* data;
-  // MID only
-  const double* stab;     // FP64 per-mode scale table (data addressing) or null
-  const T* mu_line;       // eigenvalues along the line axis, index k-1
-  const T* mu_col;        // along x, index ix
-  const T* mu_outer;      // along the outer axis (3D), index outer, or null
-  T gamma, alpha, beta2, cnorm;
-  DevState* st;
-  double* partials;
-  int scalar_mode;        // 0 none, 1 init (gamma_1), 2 MINRES iteration
-};
-
-template <typename T, bool MID>
-__global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
-  typedef typename C2<T>::t c_t;
-  if (a.st && a.st->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = 1 << a.logn, H = N >> 1;
-  c_t* A = (c_t*)smem_raw;
-  c_t* B = A + (size_t)a.C * a.LS;
-  c_t* s_tw = B + (size_t)a.C * a.LS;
-  c_t* s_scr = s_tw + H;
-  T* s_hs = (T*)(s_scr + (size_t)a.C * 32);
-  load_tables<T>(s_tw, s_hs, a.tw, a.hs, a.logn);
-  const int n = a.n, C = a.C;
-  const int ntx = (a.ncols + C - 1) / C;
-  const int ntiles = ntx * a.nouter;
-  const int nthr = blockDim.x;
-  int logC = 0;
-  while ((1 << logC) < C) ++logC;
-  double g2acc = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int o = tile / ntx;
-    const int col0 = (tile - o * ntx) * C;
-    const int Ch = min(C, a.ncols - col0);
-    const long base = (long)o * a.outer_stride + col0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < C * n; i += nthr) {
-      const int c = i & (C - 1), j = i >> logC;
-      if (c < Ch) A[(size_t)c * a.LS + j + 1] = a.data[base + (long)j * a.line_stride + c];
-    }
-    __syncthreads();
-    dst_lines<T, false>(A, B, a.LS, Ch, a.TL, a.logn, s_tw, s_hs, s_scr);
-    if (MID) {
-      // per-mode scale; gamma^2 partials = sum s |F|^2 over both blocks
-      const int l = threadIdx.x / a.TL, t = threadIdx.x - l * a.TL;
-      if (l < Ch) {
-        c_t* al = A + (size_t)l * a.LS;
-        const int ix = col0 + l;
-        T murest = a.mu_col ? a.mu_col[ix] : (T)0;
-        if (a.mu_outer) murest += a.mu_outer[o];
-        T part = (T)0;
-        for (int m = 1 + t; m <= n; m += a.TL) {
-          const int pos = dst_out_pos(m, N);
-          c_t F = al[pos];
-          T sc;
-          if (a.stab) {
-            sc = (T)a.stab[base + (long)(m - 1) * a.line_stride + l];
-          } else {
-            const T e = fma(a.gamma, murest + a.mu_line[m - 1], a.alpha);
-            sc = a.cnorm * rsq(fma(e, e, a.beta2));
-          }
-          part = fma(sc, fma(F.x, F.x, F.y * F.y), part);
-          F.x *= sc;
-          F.y *= sc;
-          al[pos] = F;
-        }
-        g2acc += (double)part;
-      }
-      __syncthreads();
-      dst_lines<T, true>(A, B, a.LS, Ch, a.TL, a.logn, s_tw, s_hs, s_scr);
-    }
-    for (int i = threadIdx.x; i < C * n; i += nthr) {
-      const int c = i & (C - 1), j = i >> logC;
-      if (c < Ch) a.data[base + (long)j * a.line_stride + c] = A[(size_t)c * a.LS + dst_out_pos(j + 1, N)];
-    }
-  }
-  if (!MID || a.scalar_mode == 0) return;
-  double v[1] = {g2acc}, tot[1];
-  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot)) return;
-  if (threadIdx.x != 0) return;
-  DevState* st = a.st;
-  if (a.scalar_mode == 1) {  // gamma_1 = sqrt(<P^{-1} r0, r0>), start of MINRES
-    const double g2 = tot[0];
-    if (!(g2 > 0.0) || !(g2 < 1e300)) {
-      st->done = 1;
-      st->status = (g2 == 0.0) ? ST_OK : ST_BREAKDOWN;
-      st->relres = (g2 == 0.0) ? 0.0 : st->relres;
-      return;
-    }
-    st->gam = sqrt(g2);
-    st->gam1 = st->gam;
-    st->gam_old = 1.0;
-    st->eta = st->gam;
-    st->eta_x = st->gam;
-    st->rho = st->bnorm / st->gam;  // exact at x_0 = 0
-    return;
-  }
-  givens_step(st, tot[0]);
-}
-
-// ---------------------------------------------------------------------------
 // Ingest: f (complex128) -> b = [Im f; Re f] (block form, Eq. 2), MINRES
 // start vectors, ||b||, and the scalar state.
 // ---------------------------------------------------------------------------
@@ -485,7 +365,7 @@ struct IngestArgs {
   int maxit;
 };
 
-__global__ void __launch_bounds__(256) k_ingest(IngestArgs a) {
+static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a) {
   double acc[1] = {0.0};
   const double2 zero = make_double2(0.0, 0.0);
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < a.M; p += (long)gridDim.x * blockDim.x) {
@@ -535,7 +415,7 @@ __global__ void __launch_bounds__(256) k_ingest(IngestArgs a) {
 // Plan set-up kernels
 // ---------------------------------------------------------------------------
 // scaled copy of one face array (a_e / h^2) and its min / max / validity
-__global__ void k_scale_faces(const double* __restrict__ src, double* __restrict__ dst, long count,
+static __global__ void k_scale_faces(const double* __restrict__ src, double* __restrict__ dst, long count,
                               double inv_h2, unsigned long long* minmax /* [min bits, max bits, bad] */) {
   unsigned long long lmin = ~0ull, lmax = 0ull, bad = 0ull;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {

@@ -1,0 +1,89 @@
+// Launch wrappers of the sine-transform passes for one real type CSL_T
+// (instantiated by csl_pass64.cu and csl_pass32.cu so that the two
+// precisions compile in parallel).
+#pragma once
+#include "csl_passes.cuh"
+
+namespace csl {
+
+template <typename T, int N>
+cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+  if (load == LOAD_V && store == STORE_T)
+    k_row<T, N, LOAD_V, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else if (load == LOAD_LANCZOS && store == STORE_T)
+    k_row<T, N, LOAD_LANCZOS, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else if (load == LOAD_T && store == STORE_Z)
+    k_row<T, N, LOAD_T, STORE_Z><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else if (load == LOAD_T && store == STORE_Z_UPDATE)
+    k_row<T, N, LOAD_T, STORE_Z_UPDATE><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else if (load == LOAD_T && store == STORE_D)
+    k_row<T, N, LOAD_T, STORE_D><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+  switch (N) {
+#define CASE(NN) \
+  case NN: return launch_row_n<T, NN>(load, store, a, L, s);
+    CSL_FOR_EACH_N(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_strided(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+  switch (N) {
+#define CASE(NN)                                                          \
+  case NN:                                                                \
+    if (mid)                                                              \
+      k_strided<T, NN, true><<<L.blocks, L.threads, L.smem, s>>>(a);      \
+    else                                                                  \
+      k_strided<T, NN, false><<<L.blocks, L.threads, L.smem, s>>>(a);     \
+    return cudaGetLastError();
+    CSL_FOR_EACH_N(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// dynamic shared memory limit of one kernel = opt-in maximum - its static shared memory
+inline cudaError_t allow_dyn_smem(const void* k) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+template <typename T>
+cudaError_t set_pass_attrs() {
+  cudaError_t e = cudaSuccess;
+#define SETA(k) \
+  if (e == cudaSuccess) e = allow_dyn_smem((const void*)k);
+#define CASE(NN)                                    \
+  SETA((k_row<T, NN, LOAD_V, STORE_T>))             \
+  SETA((k_row<T, NN, LOAD_LANCZOS, STORE_T>))       \
+  SETA((k_row<T, NN, LOAD_T, STORE_Z>))             \
+  SETA((k_row<T, NN, LOAD_T, STORE_Z_UPDATE>))      \
+  SETA((k_row<T, NN, LOAD_T, STORE_D>))             \
+  SETA((k_strided<T, NN, true>))                    \
+  SETA((k_strided<T, NN, false>))
+  CSL_FOR_EACH_N(CASE)
+#undef CASE
+#undef SETA
+  return e;
+}
+
+template cudaError_t launch_row<CSL_T>(int, int, int, const RowArgs<CSL_T>&, const PassLaunch&, cudaStream_t);
+template cudaError_t launch_strided<CSL_T>(int, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
+                                           cudaStream_t);
+template cudaError_t set_pass_attrs<CSL_T>();
+
+}  // namespace csl

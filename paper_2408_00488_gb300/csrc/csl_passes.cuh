@@ -1,0 +1,341 @@
+// Sine-transform passes of P^{-1} (Eq. 4 via Section 2.3) with the MINRES
+// vector work fused into the first and last pass.
+//
+//   k_row     DST along x (contiguous rows).  Each warp owns 32/TPL rows: it
+//             loads them (fusing v_{j+1} = u' - (delta_j/gamma_j) v_j when
+//             LOAD_LANCZOS), transforms them in shared memory and stores them
+//             (fusing z_{j+1} and the w/x update when STORE_Z_UPDATE).
+//   k_strided DST along y or z: a CTA loads a tile of adjacent columns (one
+//             line per column), each warp transforms its lines; with MID the
+//             forward transform, per-mode scale, gamma^2 partial sums
+//             (Parseval: <P^{-1}v, v> = sum_k s_k |S v|_k^2) and inverse
+//             transform all happen in shared memory, and the last CTA runs
+//             the Givens step.
+#pragma once
+#include "csl_common.cuh"
+#include "csl_fft.cuh"
+#include "csl_kernels.cuh"
+
+namespace csl {
+
+enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2 };
+enum { STORE_T = 0, STORE_D = 1, STORE_Z = 2, STORE_Z_UPDATE = 3 };
+
+template <typename T>
+struct RowArgs {
+  int n, nrows;
+  const typename C2<T>::t* tw;
+  const T* hs;
+  const double2* vin;             // LOAD_V
+  const typename C2<T>::t* tin;   // LOAD_T
+  double2* vnew;                  // LOAD_LANCZOS: u' in, v_{j+1} out
+  const double2* vcur;            // LOAD_LANCZOS: v_j
+  typename C2<T>::t* tout;        // STORE_T
+  double2* dout;                  // STORE_D
+  typename C2<T>::t* zout;        // STORE_Z*: z_{j+1}
+  const typename C2<T>::t* zcur;  // STORE_Z_UPDATE: z_j
+  double2* wprev;                 // in w_{j-1}, out w_{j+1}
+  const double2* wcur;            // w_j
+  double2* x;
+  DevState* st;                   // may be null (precondition only)
+};
+
+template <typename T>
+struct StridedArgs {
+  int n, ncols, nouter;
+  long outer_stride, line_stride;
+  const typename C2<T>::t* tw;
+  const T* hs;
+  typename C2<T>::t* data;
+  // MID only
+  const double* stab;  // FP64 per-mode scale table (data addressing) or null
+  const T* mu_line;    // eigenvalues along the line axis, index k-1
+  const T* mu_col;     // along x, index ix
+  const T* mu_outer;   // along the outer axis (3D), index outer, or null
+  T gamma, alpha, beta2, cnorm;
+  DevState* st;
+  double* partials;
+  int scalar_mode;     // 0 none, 1 init (gamma_1), 2 MINRES iteration
+};
+
+// byte offsets of the shared-memory regions: twiddles | half sines | lines
+template <typename T, int N>
+__host__ __device__ constexpr size_t pass_tables_bytes() {
+  return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16;
+}
+template <typename T, int N>
+__host__ __device__ constexpr size_t pass_smem_bytes(int lines) {
+  return pass_tables_bytes<T, N>() + (size_t)lines * dst_line_stride<N>() * sizeof(typename C2<T>::t);
+}
+
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+
+template <typename T, int N, int LOAD, int STORE>
+__global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
+  typedef typename C2<T>::t c_t;
+  constexpr int TPL = DstShape<N>::TPL, LPW = 32 / TPL, LS = dst_line_stride<N>();
+  constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
+  constexpr int UB = NL < 8 ? NL : 8;      // load batch
+  if (a.st && a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c_t* s_tw = (c_t*)smem_raw;
+  T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
+  c_t* lines = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  load_tables<T>(s_tw, s_hs, a.tw, a.hs, N);
+  double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
+  if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
+  if (STORE == STORE_Z_UPDATE) {
+    wa = a.st->w_a;
+    wb = a.st->w_b;
+    wc = a.st->w_c;
+    xc = a.st->x_coef;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / TPL, t = lane - sub * TPL;
+  const int lpb = (blockDim.x >> 5) * LPW;
+  c_t* line = lines + (size_t)(warp * LPW + sub) * LS;
+  const int n = a.n;
+  for (int row0 = blockIdx.x * lpb; row0 < a.nrows; row0 += gridDim.x * lpb) {
+    const int row = row0 + warp * LPW + sub;
+    const bool valid = row < a.nrows;
+    const long base = (long)row * n;
+    // global loads in batches of UB elements per lane, all issued before use
+#pragma unroll
+    for (int i0 = 0; i0 < NL; i0 += UB) {
+      if (LOAD == LOAD_LANCZOS) {
+        double2 u[UB], vc[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          if (valid && j < n) {
+            u[k] = a.vnew[base + j];
+            vc[k] = a.vcur[base + j];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          if (j < n) {
+            c_t val = mkc<T>((T)0, (T)0);
+            if (valid) {
+              const double2 vn = make_double2(fma(-lz, vc[k].x, u[k].x), fma(-lz, vc[k].y, u[k].y));
+              a.vnew[base + j] = vn;
+              val = from_d2<T>(vn);
+            }
+            line[j + 1] = val;
+          }
+        }
+      } else {
+        c_t val[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          val[k] = mkc<T>((T)0, (T)0);
+          if (valid && j < n) val[k] = (LOAD == LOAD_V) ? from_d2<T>(a.vin[base + j]) : a.tin[base + j];
+        }
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          if (j < n) line[j + 1] = val[k];
+        }
+      }
+    }
+    __syncwarp();
+    dst_line<T, N, false>(line, t, s_tw, s_hs);
+    if (valid) {
+#pragma unroll
+      for (int i0 = 0; i0 < NL; i0 += UB) {
+        if (STORE == STORE_Z_UPDATE) {
+          c_t zo[UB];
+          double2 wp[UB], wq[UB], xo[UB];
+#pragma unroll
+          for (int k = 0; k < UB; ++k) {
+            const int j = t + TPL * (i0 + k);
+            if (j < n) {
+              zo[k] = a.zcur[base + j];
+              wp[k] = a.wprev[base + j];
+              wq[k] = a.wcur[base + j];
+              xo[k] = a.x[base + j];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < UB; ++k) {
+            const int j = t + TPL * (i0 + k);
+            if (j < n) {
+              const long p = base + j;
+              a.zout[p] = line[dst_out_pos<N>(j + 1)];
+              const double2 zd = to_d2(zo[k]);
+              const double2 wn = make_double2(fma(wa, zd.x, fma(wb, wp[k].x, wc * wq[k].x)),
+                                              fma(wa, zd.y, fma(wb, wp[k].y, wc * wq[k].y)));
+              a.wprev[p] = wn;
+              a.x[p] = make_double2(fma(xc, wn.x, xo[k].x), fma(xc, wn.y, xo[k].y));
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < UB; ++k) {
+            const int j = t + TPL * (i0 + k);
+            if (j < n) {
+              const long p = base + j;
+              const c_t F = line[dst_out_pos<N>(j + 1)];
+              if (STORE == STORE_T)
+                a.tout[p] = F;
+              else if (STORE == STORE_D)
+                a.dout[p] = to_d2(F);
+              else
+                a.zout[p] = F;
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N, bool MID>
+__global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
+  typedef typename C2<T>::t c_t;
+  constexpr int TPL = DstShape<N>::TPL, LPW = 32 / TPL, LS = dst_line_stride<N>();
+  constexpr int NL = (N + TPL - 1) / TPL;
+  constexpr int UB = NL < 8 ? NL : 8;
+  if (a.st && a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c_t* s_tw = (c_t*)smem_raw;
+  T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
+  c_t* lines = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  load_tables<T>(s_tw, s_hs, a.tw, a.hs, N);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / TPL, t = lane - sub * TPL;
+  const int C = (blockDim.x >> 5) * LPW;  // lines (columns) per tile, a power of two
+  int logC = 0;
+  while ((1 << logC) < C) ++logC;
+  const int myl = warp * LPW + sub;
+  c_t* line = lines + (size_t)myl * LS;
+  const int n = a.n;
+  const int ntx = (a.ncols + C - 1) / C;
+  const int ntiles = ntx * a.nouter;
+  double g2acc = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int o = tile / ntx;
+    const int col0 = (tile - o * ntx) * C;
+    const int Ch = min(C, a.ncols - col0);
+    const long base = (long)o * a.outer_stride + col0;
+    __syncthreads();  // tables loaded / previous tile stored
+    // blockDim = C * TPL, so NL rounds per thread cover the C x n tile; loads
+    // are batched UB at a time so that they are all in flight together
+#pragma unroll
+    for (int q0 = 0; q0 < NL; q0 += UB) {
+      c_t v[UB];
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        const int e = threadIdx.x + blockDim.x * (q0 + k);
+        const int c = e & (C - 1), j = e >> logC;
+        v[k] = (c < Ch && j < n) ? a.data[base + (long)j * a.line_stride + c] : mkc<T>((T)0, (T)0);
+      }
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        const int e = threadIdx.x + blockDim.x * (q0 + k);
+        const int c = e & (C - 1), j = e >> logC;
+        if (j < n) lines[(size_t)c * LS + j + 1] = v[k];
+      }
+    }
+    __syncthreads();
+    dst_line<T, N, false>(line, t, s_tw, s_hs);
+    if (MID) {
+      if (myl < Ch) {
+        const int ix = col0 + myl;
+        T murest = a.mu_col ? a.mu_col[ix] : (T)0;
+        if (a.mu_outer) murest += a.mu_outer[o];
+        T part = (T)0;
+        for (int m = 1 + t; m <= n; m += TPL) {
+          const int pos = dst_out_pos<N>(m);
+          c_t F = line[pos];
+          T sc;
+          if (a.stab) {
+            sc = (T)a.stab[base + (long)(m - 1) * a.line_stride + myl];
+          } else {
+            const T e = fma(a.gamma, murest + a.mu_line[m - 1], a.alpha);
+            sc = a.cnorm * rsq(fma(e, e, a.beta2));
+          }
+          part = fma(sc, fma(F.x, F.x, F.y * F.y), part);
+          F.x *= sc;
+          F.y *= sc;
+          line[pos] = F;
+        }
+        g2acc += (double)part;
+      }
+      __syncwarp();
+      dst_line<T, N, true>(line, t, s_tw, s_hs);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C * n; i += blockDim.x) {
+      const int c = i & (C - 1), j = i >> logC;
+      if (c < Ch) a.data[base + (long)j * a.line_stride + c] = lines[(size_t)c * LS + dst_out_pos<N>(j + 1)];
+    }
+  }
+  if (!MID || a.scalar_mode == 0) return;
+  double v[1] = {g2acc}, tot[1];
+  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot)) return;
+  if (threadIdx.x != 0) return;
+  DevState* st = a.st;
+  if (a.scalar_mode == 1) {  // gamma_1 = sqrt(<P^{-1} r0, r0>), start of MINRES
+    const double g2 = tot[0];
+    if (!(g2 > 0.0) || !(g2 < 1e300)) {
+      st->done = 1;
+      st->status = (g2 == 0.0) ? ST_OK : ST_BREAKDOWN;
+      st->relres = (g2 == 0.0) ? 0.0 : st->relres;
+      return;
+    }
+    st->gam = sqrt(g2);
+    st->gam1 = st->gam;
+    st->gam_old = 1.0;
+    st->eta = st->gam;
+    st->eta_x = st->gam;
+    st->rho = st->bnorm / st->gam;  // exact at x_0 = 0
+    return;
+  }
+  givens_step(st, tot[0]);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch over the transform length (one instantiation per N).
+// ---------------------------------------------------------------------------
+struct PassLaunch {
+  int blocks, threads;
+  size_t smem;
+};
+
+#define CSL_FOR_EACH_N(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+template <typename T>
+size_t pass_smem(int N, int lines) {
+  switch (N) {
+#define CASE(NN) \
+  case NN: return pass_smem_bytes<T, NN>(lines);
+    CSL_FOR_EACH_N(CASE)
+#undef CASE
+  }
+  return 0;
+}
+
+inline int pass_tpl(int N) {
+  switch (N) {
+#define CASE(NN) \
+  case NN: return DstShape<NN>::TPL;
+    CSL_FOR_EACH_N(CASE)
+#undef CASE
+  }
+  return 1;
+}
+
+template <typename T>
+cudaError_t launch_row(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_strided(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s);
+template <typename T>
+cudaError_t set_pass_attrs();
+
+}  // namespace csl
