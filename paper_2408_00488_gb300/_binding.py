@@ -275,3 +275,4 @@ class Plan:
         _check(lib.csl_coef_grad(self._h, _dptr(z, ("complex128",), "z"), _dptr(y, ("complex128",), "y"),
                                  ptrs), "csl_coef_grad")
         return tuple(grads)
+

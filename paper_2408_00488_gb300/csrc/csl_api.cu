@@ -58,6 +58,40 @@ int ilog2_exact(long v) {
   return l;
 }
 
+// exp(-2 pi i num/den) as interleaved (re, im)
+void push_root(std::vector<double>& out, long num, long den) {
+  const double a = 2.0 * M_PI * (double)(num % den) / (double)den;
+  out.push_back(cos(a));
+  out.push_back(-sin(a));
+}
+
+// The extra twiddle table of a transform of length N (LineDst::TP entries):
+// four-step lines (64 <= N <= 256): [k1][g] = w_N^{g k1}, k1 < R1, g < R2;
+// wide lines (N >= 512): the Stockham passes 2 and 3, [q][k] = w_{Ls r}^{q k}.
+void make_tp_table(int N, std::vector<double>& out) {
+  out.clear();
+  int R0 = 0, R1 = 0, R2 = 0;
+  switch (N) {
+    case 64: R1 = DstShape<64>::R1; R2 = DstShape<64>::R2; break;
+    case 128: R1 = DstShape<128>::R1; R2 = DstShape<128>::R2; break;
+    case 256: R1 = DstShape<256>::R1; R2 = DstShape<256>::R2; break;
+    case 512: R0 = WideShape<512>::R0; R1 = WideShape<512>::R1; R2 = WideShape<512>::R2; break;
+    case 1024: R0 = WideShape<1024>::R0; R1 = WideShape<1024>::R1; R2 = WideShape<1024>::R2; break;
+    default: return;
+  }
+  if (N < 512) {
+    for (int k1 = 0; k1 < R1; ++k1)
+      for (int g = 0; g < R2; ++g) push_root(out, (long)g * k1, N);
+    return;
+  }
+  const int passes[2][2] = {{R0, R1}, {R0 * R1, R2}};  // (Ls, r) of passes 2 and 3
+  for (int p = 0; p < 2; ++p) {
+    const int Ls = passes[p][0], r = passes[p][1];
+    for (int q = 0; q < r; ++q)
+      for (int k = 0; k < Ls; ++k) push_root(out, (long)q * k, (long)Ls * r);
+  }
+}
+
 }  // namespace
 
 struct csl_plan {
@@ -77,6 +111,7 @@ struct csl_plan {
   float* mu_f[3] = {nullptr, nullptr, nullptr};
   void* tw[3] = {nullptr, nullptr, nullptr};
   void* hs[3] = {nullptr, nullptr, nullptr};
+  void* tp[3] = {nullptr, nullptr, nullptr};
   double2 *b = nullptr, *x = nullptr, *io = nullptr;
   double2* v[2] = {nullptr, nullptr};
   double2* w[2] = {nullptr, nullptr};
@@ -135,7 +170,7 @@ template <typename T>
 void choose_cta(PassCfg& c, int want_threads) {
   const int tpl = pass_tpl(c.N);
   int threads = want_threads;
-  while (threads > 32 && pass_smem<T>(c.N, threads / tpl) > 100 * 1024) threads >>= 1;
+  while (threads > 32 && threads > tpl && pass_smem<T>(c.N, threads / tpl) > 100 * 1024) threads >>= 1;
   c.lines = threads / tpl;
   c.L.threads = threads;
   c.L.smem = pass_smem<T>(c.N, c.lines);
@@ -173,7 +208,7 @@ void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride,
     if (threads > 1024) threads = 1024;
   }
   // no wider than the grid's x extent needs
-  while (threads > 32 && (threads / tpl) / 2 >= ncols) threads >>= 1;
+  while (threads > 32 && threads > tpl && (threads / tpl) / 2 >= ncols) threads >>= 1;
   // few tiles: smaller CTAs so that every SM gets work
   while (want_lines <= 0 && threads > 32 && threads / tpl > 2 &&
          (long)((ncols + threads / tpl - 1) / (threads / tpl)) * nouter < 2 * kSMs)
@@ -192,6 +227,7 @@ RowArgs<T> row_args(csl_plan* P) {
   a.nrows = P->row.nouter;
   a.tw = (const typename C2<T>::t*)P->tw[0];
   a.hs = (const T*)P->hs[0];
+  a.tp = (const typename C2<T>::t*)P->tp[0];
   return a;
 }
 
@@ -206,6 +242,7 @@ StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
   a.line_stride = c.line_stride;
   a.tw = (const typename C2<T>::t*)P->tw[axis];
   a.hs = (const T*)P->hs[axis];
+  a.tp = (const typename C2<T>::t*)P->tp[axis];
   a.data = (typename C2<T>::t*)P->T;
   return a;
 }
@@ -544,6 +581,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     P->mu_f[d] = (float*)dalloc(P, (size_t)P->n[d] * 4, &err);
     P->tw[d] = dalloc(P, (size_t)(N / 2) * 2 * tsz, &err);
     P->hs[d] = dalloc(P, (size_t)(N / 2 + 1) * tsz, &err);
+    P->tp[d] = dalloc(P, (size_t)(line_tp_size(N) + 1) * 2 * tsz, &err);
   }
   P->b = (double2*)dalloc(P, M * 16, &err);
   P->x = (double2*)dalloc(P, M * 16, &err);
@@ -637,6 +675,19 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     }
     for (int j = 0; j <= N / 2; ++j) hsd[j] = 0.5 * sin(M_PI * (double)j / N);
     hsd[N / 2] = 0.5;
+    std::vector<double> tpd;
+    make_tp_table(N, tpd);
+    const size_t ntp = tpd.size();
+    if (ntp) {
+      if (o.precision == CSL_PREC_FP32) {
+        std::vector<float> tpf(ntp);
+        for (size_t i = 0; i < ntp; ++i) tpf[i] = (float)tpd[i];
+        err = cudaMemcpy(P->tp[d], tpf.data(), ntp * 4, cudaMemcpyHostToDevice);
+      } else {
+        err = cudaMemcpy(P->tp[d], tpd.data(), ntp * 8, cudaMemcpyHostToDevice);
+      }
+      if (err != cudaSuccess) break;
+    }
     err = cudaMemcpy(P->mu_d[d], mu.data(), nd * 8, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(P->mu_f[d], muf.data(), nd * 4, cudaMemcpyHostToDevice);
     if (o.precision == CSL_PREC_FP32) {

@@ -22,8 +22,25 @@ __device__ __forceinline__ typename C2<T>::t mkc(T x, T y) {
   return r;
 }
 
+// Exact float -> double by moving the sign, exponent and mantissa fields with
+// integer instructions.  On GB300 the hardware conversion issues on the FP64
+// pipe (about two per SM per clock), which the FP64 stencil and vector
+// updates already saturate; the integer pipe is idle.  Zero, infinities and
+// NaN are handled; subnormal floats (exponent field 0) take the hardware path.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) {
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const unsigned ex = (e == 255u) ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
+  const unsigned hi = (u & 0x80000000u) | (ex << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(f2d_exact(v.x), f2d_exact(v.y)); }
 template <typename T> __device__ __forceinline__ typename C2<T>::t from_d2(double2 v);
 template <> __device__ __forceinline__ double2 from_d2<double>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 from_d2<float>(double2 v) {

@@ -26,6 +26,7 @@ struct RowArgs {
   int n, nrows;
   const typename C2<T>::t* tw;
   const T* hs;
+  const typename C2<T>::t* tp;    // extra twiddle table (LineDst::TP entries)
   const double2* vin;             // LOAD_V
   const typename C2<T>::t* tin;   // LOAD_T
   double2* vnew;                  // LOAD_LANCZOS: u' in, v_{j+1} out
@@ -46,6 +47,7 @@ struct StridedArgs {
   long outer_stride, line_stride;
   const typename C2<T>::t* tw;
   const T* hs;
+  const typename C2<T>::t* tp;
   typename C2<T>::t* data;
   // MID only
   const double* stab;  // FP64 per-mode scale table (data addressing) or null
@@ -58,14 +60,17 @@ struct StridedArgs {
   int scalar_mode;     // 0 none, 1 init (gamma_1), 2 MINRES iteration
 };
 
-// byte offsets of the shared-memory regions: twiddles | half sines | lines
+// byte offsets of the shared-memory regions: twiddles | half sines | extra
+// twiddles | scan scratch (2 per line) | lines
 template <typename T, int N>
 __host__ __device__ constexpr size_t pass_tables_bytes() {
-  return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16;
+  return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16 +
+         (size_t)line_tp_size(N) * sizeof(typename C2<T>::t);
 }
 template <typename T, int N>
 __host__ __device__ constexpr size_t pass_smem_bytes(int lines) {
-  return pass_tables_bytes<T, N>() + (size_t)lines * dst_line_stride<N>() * sizeof(typename C2<T>::t);
+  return pass_tables_bytes<T, N>() + (size_t)lines * 2 * sizeof(typename C2<T>::t) +
+         (size_t)lines * LineDst<T, N>::LS * sizeof(typename C2<T>::t);
 }
 
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
@@ -74,15 +79,19 @@ __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 template <typename T, int N, int LOAD, int STORE>
 __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
   typedef typename C2<T>::t c_t;
-  constexpr int TPL = DstShape<N>::TPL, LPW = 32 / TPL, LS = dst_line_stride<N>();
+  typedef LineDst<T, N> D;
+  constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
   constexpr int UB = NL < 8 ? NL : 8;      // load batch
   if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* s_tw = (c_t*)smem_raw;
   T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
-  c_t* lines = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
-  load_tables<T>(s_tw, s_hs, a.tw, a.hs, N);
+  c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  const int nlines = blockDim.x / TPL;
+  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  c_t* lines = s_scr + 2 * nlines;
+  load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
   if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
   if (STORE == STORE_Z_UPDATE) {
@@ -92,13 +101,12 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
     xc = a.st->x_coef;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / TPL, t = lane - sub * TPL;
-  const int lpb = (blockDim.x >> 5) * LPW;
-  c_t* line = lines + (size_t)(warp * LPW + sub) * LS;
+  const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
+  const int lpb = nlines;
+  c_t* line = lines + (size_t)myl * LS;
   const int n = a.n;
   for (int row0 = blockIdx.x * lpb; row0 < a.nrows; row0 += gridDim.x * lpb) {
-    const int row = row0 + warp * LPW + sub;
+    const int row = row0 + myl;
     const bool valid = row < a.nrows;
     const long base = (long)row * n;
     // global loads in batches of UB elements per lane, all issued before use
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
               a.vnew[base + j] = vn;
               val = from_d2<T>(vn);
             }
-            line[j + 1] = val;
+            line[D::in_pos(j + 1)] = val;
           }
         }
       } else {
@@ -138,12 +146,12 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
 #pragma unroll
         for (int k = 0; k < UB; ++k) {
           const int j = t + TPL * (i0 + k);
-          if (j < n) line[j + 1] = val[k];
+          if (j < n) line[D::in_pos(j + 1)] = val[k];
         }
       }
     }
-    __syncwarp();
-    dst_line<T, N, false>(line, t, s_tw, s_hs);
+    D::line_sync();
+    D::template run<false>(line, t, s_tw, s_hs, s_tp, s_scr);
     if (valid) {
 #pragma unroll
       for (int i0 = 0; i0 < NL; i0 += UB) {
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
             const int j = t + TPL * (i0 + k);
             if (j < n) {
               const long p = base + j;
-              a.zout[p] = line[dst_out_pos<N>(j + 1)];
+              a.zout[p] = line[D::out_pos(j + 1)];
               const double2 zd = to_d2(zo[k]);
               const double2 wn = make_double2(fma(wa, zd.x, fma(wb, wp[k].x, wc * wq[k].x)),
                                               fma(wa, zd.y, fma(wb, wp[k].y, wc * wq[k].y)));
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
             const int j = t + TPL * (i0 + k);
             if (j < n) {
               const long p = base + j;
-              const c_t F = line[dst_out_pos<N>(j + 1)];
+              const c_t F = line[D::out_pos(j + 1)];
               if (STORE == STORE_T)
                 a.tout[p] = F;
               else if (STORE == STORE_D)
@@ -191,28 +199,29 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
         }
       }
     }
-    __syncwarp();
+    D::line_sync();
   }
 }
 
 template <typename T, int N, bool MID>
 __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
   typedef typename C2<T>::t c_t;
-  constexpr int TPL = DstShape<N>::TPL, LPW = 32 / TPL, LS = dst_line_stride<N>();
+  typedef LineDst<T, N> D;
+  constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;
   constexpr int UB = NL < 8 ? NL : 8;
   if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* s_tw = (c_t*)smem_raw;
   T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
-  c_t* lines = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
-  load_tables<T>(s_tw, s_hs, a.tw, a.hs, N);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / TPL, t = lane - sub * TPL;
-  const int C = (blockDim.x >> 5) * LPW;  // lines (columns) per tile, a power of two
+  c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  const int C = blockDim.x / TPL;  // lines (columns) per tile, a power of two
+  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  c_t* lines = s_scr + 2 * C;
+  load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   int logC = 0;
   while ((1 << logC) < C) ++logC;
-  const int myl = warp * LPW + sub;
+  const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
   c_t* line = lines + (size_t)myl * LS;
   const int n = a.n;
   const int ntx = (a.ncols + C - 1) / C;
@@ -239,11 +248,11 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
       for (int k = 0; k < UB; ++k) {
         const int e = threadIdx.x + blockDim.x * (q0 + k);
         const int c = e & (C - 1), j = e >> logC;
-        if (j < n) lines[(size_t)c * LS + j + 1] = v[k];
+        if (j < n) lines[(size_t)c * LS + D::in_pos(j + 1)] = v[k];
       }
     }
     __syncthreads();
-    dst_line<T, N, false>(line, t, s_tw, s_hs);
+    D::template run<false>(line, t, s_tw, s_hs, s_tp, s_scr);
     if (MID) {
       if (myl < Ch) {
         const int ix = col0 + myl;
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
         if (a.mu_outer) murest += a.mu_outer[o];
         T part = (T)0;
         for (int m = 1 + t; m <= n; m += TPL) {
-          const int pos = dst_out_pos<N>(m);
+          const int pos = D::out_pos(m);
           c_t F = line[pos];
           T sc;
           if (a.stab) {
@@ -267,13 +276,13 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
         }
         g2acc += (double)part;
       }
-      __syncwarp();
-      dst_line<T, N, true>(line, t, s_tw, s_hs);
+      D::line_sync();
+      D::template run<true>(line, t, s_tw, s_hs, s_tp, s_scr);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < C * n; i += blockDim.x) {
       const int c = i & (C - 1), j = i >> logC;
-      if (c < Ch) a.data[base + (long)j * a.line_stride + c] = lines[(size_t)c * LS + dst_out_pos<N>(j + 1)];
+      if (c < Ch) a.data[base + (long)j * a.line_stride + c] = lines[(size_t)c * LS + D::out_pos(j + 1)];
     }
   }
   if (!MID || a.scalar_mode == 0) return;
@@ -324,7 +333,7 @@ size_t pass_smem(int N, int lines) {
 inline int pass_tpl(int N) {
   switch (N) {
 #define CASE(NN) \
-  case NN: return DstShape<NN>::TPL;
+  case NN: return LineDst<float, NN>::TPL;
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
