@@ -176,6 +176,29 @@ csl_status csl_coef_grad(csl_plan* plan, const double* z, const double* y,
                          double* const grad_faces[3]);
 
 /*
+ * Allocation-free P^{-1} v (the paper has no counterpart; a deployment
+ * convenience).  Same result as csl_precondition on a plan built with the
+ * same grid, gamma, alpha, beta and precision, but without a plan and without
+ * allocating: for callers that cannot call cudaMalloc (a memory-pool-managed
+ * runtime that owns all device memory, a fixed-budget embedded service, or
+ * code running while a stream is being captured).
+ *   dim, n[3]   grid (n[d] + 1 a power of two in [4, 1024]); at most 262144
+ *               grid points (e.g. 511 x 511, 63 x 63 x 63), else
+ *               CSL_UNSUPPORTED_SIZE with a message in csl_last_error()
+ *   gamma       the averaged coefficient of Eq. 4 (> 0); alpha, beta: lambda
+ *   precision   CSL_PREC_FP64 or CSL_PREC_FP32 (as csl_plan_options.precision)
+ *   v, out      device block-pair (or complex128) vectors of the grid; may alias
+ *   stream      cudaStream_t as void*; the call is stream-ordered, asynchronous
+ * Scratch (about 6 MiB) lives in static device arrays of the library, held by
+ * every GPU that loads it until the process exits and shared by all calls:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * The first call on a device performs a one-time set-up (looking up the
+ * arrays' device addresses) and should come before any stream capture.
+ */
+csl_status csl_precondition_static(int dim, const int64_t n[3], double gamma, double alpha, double beta,
+                                   int precision, const double* v, double* out, void* stream);
+
+/*
  * Measurement hook (not part of the method): time each kernel of one MINRES
  * iteration on the plan's stream with CUDA events, `reps` launches each,
  * against a scratch copy of the solver state so that no kernel exits early.

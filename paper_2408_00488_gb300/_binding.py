@@ -49,6 +49,8 @@ _SIGS = {
     "csl_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
     "csl_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
     "csl_coef_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "csl_precondition_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
     "csl_time_kernels": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]),
 }
@@ -276,3 +278,20 @@ class Plan:
                                  ptrs), "csl_coef_grad")
         return tuple(grads)
 
+
+def precondition_static(v, gamma: float, lam: complex, precision: str = "fp64", out=None, stream=None):
+    """P^{-1} v without a plan and without any device allocation
+    (csl_precondition_static): for callers that cannot allocate device memory.
+    v: complex128 CUDA tensor of the grid's shape (2D or 3D, at most 262144
+    points); gamma: the averaged coefficient of P; lam: the shift."""
+    torch = _torch()
+    dim = v.dim()
+    shape = tuple(v.shape)
+    n = (ctypes.c_int64 * 3)(*(list(reversed(shape)) + [1] * (3 - dim)))
+    y = torch.empty_like(v) if out is None else out
+    lam = complex(lam)
+    st = lib.csl_precondition_static(dim, n, float(gamma), lam.real, lam.imag, _PREC[precision],
+                                     _dptr(v, ("complex128", "float64"), "v"), _dptr(y, ("complex128", "float64"), "out"),
+                                     _stream_handle(stream))
+    _check(st, "csl_precondition_static")
+    return y

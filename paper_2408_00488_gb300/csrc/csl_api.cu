@@ -506,6 +506,13 @@ const char* csl_version(void) { return "csl 0.2 (sm_103a)"; }
 
 const char* csl_last_error(void) { return g_last_error; }
 
+}  // extern "C"
+
+// message for csl_last_error() from the other translation units of the library
+void csl_internal_set_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+extern "C" {
+
 const char* csl_status_string(csl_status s) {
   switch (s) {
     case CSL_OK: return "CSL_OK";
