@@ -72,7 +72,10 @@ typedef struct csl_plan_options {
   int lines_per_cta;      /* sine-transform lines per CTA for the strided passes; 0 = tuned */
   int use_graph;          /* 1 (default): the iteration loop runs as a CUDA graph with a
                              device-controlled WHILE node; 0: host-driven loop              */
-  int reserved[8];
+  int autotune;           /* 1 (default): time the candidate CTA shapes and transform
+                             variants of each pass at plan creation and keep the fastest
+                             (cached per shape for the process); 0: built-in defaults      */
+  int reserved[7];
 } csl_plan_options;
 
 typedef struct csl_solve_info {
@@ -118,6 +121,9 @@ csl_status csl_plan_set_stream(csl_plan* plan, void* stream);
 
 /* Device bytes owned by the plan. */
 size_t csl_plan_workspace_bytes(const csl_plan* plan);
+
+/* Human-readable launch configuration the plan chose (autotuned or default). */
+const char* csl_plan_config(const csl_plan* plan);
 
 /* gamma actually used by P (Eq. 4). */
 double csl_plan_gamma(const csl_plan* plan);

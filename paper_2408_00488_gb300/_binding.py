@@ -20,7 +20,7 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32}
 class PlanOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gamma_override", ctypes.c_double),
                 ("lines_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -43,6 +43,7 @@ _SIGS = {
     "csl_plan_set_stream": (ctypes.c_int, [_P, _P]),
     "csl_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
     "csl_plan_gamma": (ctypes.c_double, [_P]),
+    "csl_plan_config": (ctypes.c_char_p, [_P]),
     "csl_apply": (ctypes.c_int, [_P, _P, _P]),
     "csl_precondition": (ctypes.c_int, [_P, _P, _P]),
     "csl_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
@@ -143,7 +144,7 @@ class Plan:
 
     def __init__(self, faces: Sequence, lam: complex, precision: str = "fp64",
                  gamma: Optional[float] = None, lines_per_cta: int = 0, use_graph: bool = True,
-                 stream=None):
+                 autotune: bool = True, stream=None):
         torch = _torch()
         dim = len(faces)
         if dim not in (2, 3):
@@ -167,6 +168,7 @@ class Plan:
         opt.gamma_override = float(gamma) if gamma is not None else float("nan")
         opt.lines_per_cta = int(lines_per_cta)
         opt.use_graph = 1 if use_graph else 0
+        opt.autotune = 1 if autotune else 0
         self.precision = precision
         h = _P()
         st = lib.csl_plan_create(ctypes.byref(h), dim, n, ptrs, self.lam.real, self.lam.imag,
@@ -199,6 +201,11 @@ class Plan:
     @property
     def gamma(self) -> float:
         return lib.csl_plan_gamma(self._h)
+
+    @property
+    def config(self) -> str:
+        """Launch configuration chosen for this plan (autotuned or default)."""
+        return lib.csl_plan_config(self._h).decode()
 
     @property
     def workspace_bytes(self) -> int:

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -46,6 +48,7 @@ const double kNaN = __builtin_nan("");
 // one sine-transform pass: line length N = n + 1, CTA shape and grid
 struct PassCfg {
   int N = 0, n = 0, lines = 0;  // lines per CTA
+  bool wide = false;             // two-warp Stockham transform (N = 512, 1024) instead of warp per line
   int ncols = 0, nouter = 0;     // strided: x extent and outer blocks; row: nouter = rows
   long outer_stride = 0, line_stride = 0;
   PassLaunch L = {1, 32, 0};
@@ -65,26 +68,28 @@ void push_root(std::vector<double>& out, long num, long den) {
   out.push_back(-sin(a));
 }
 
-// The extra twiddle table of a transform of length N (LineDst::TP entries):
-// four-step lines (64 <= N <= 256): [k1][g] = w_N^{g k1}, k1 < R1, g < R2;
-// wide lines (N >= 512): the Stockham passes 2 and 3, [q][k] = w_{Ls r}^{q k}.
+// The extra twiddle tables of a transform of length N: first the four-step
+// table of the warp-per-line path (N >= 64: [k1][g] = w_N^{g k1}, k1 < R1,
+// g < R2; line_tp_size(N, false) entries), then, for N = 512 and 1024, the
+// Stockham passes 2 and 3 of the two-warp path ([q][k] = w_{Ls r}^{q k}).
 void make_tp_table(int N, std::vector<double>& out) {
   out.clear();
-  int R0 = 0, R1 = 0, R2 = 0;
+  int R1 = 0, R2 = 0;
   switch (N) {
     case 64: R1 = DstShape<64>::R1; R2 = DstShape<64>::R2; break;
     case 128: R1 = DstShape<128>::R1; R2 = DstShape<128>::R2; break;
     case 256: R1 = DstShape<256>::R1; R2 = DstShape<256>::R2; break;
-    case 512: R0 = WideShape<512>::R0; R1 = WideShape<512>::R1; R2 = WideShape<512>::R2; break;
-    case 1024: R0 = WideShape<1024>::R0; R1 = WideShape<1024>::R1; R2 = WideShape<1024>::R2; break;
+    case 512: R1 = DstShape<512>::R1; R2 = DstShape<512>::R2; break;
+    case 1024: R1 = DstShape<1024>::R1; R2 = DstShape<1024>::R2; break;
     default: return;
   }
-  if (N < 512) {
-    for (int k1 = 0; k1 < R1; ++k1)
-      for (int g = 0; g < R2; ++g) push_root(out, (long)g * k1, N);
-    return;
-  }
-  const int passes[2][2] = {{R0, R1}, {R0 * R1, R2}};  // (Ls, r) of passes 2 and 3
+  for (int k1 = 0; k1 < R1; ++k1)
+    for (int g = 0; g < R2; ++g) push_root(out, (long)g * k1, N);
+  if (N < 512) return;
+  const int R0 = N == 1024 ? WideShape<1024>::R0 : WideShape<512>::R0;
+  const int W1 = N == 1024 ? WideShape<1024>::R1 : WideShape<512>::R1;
+  const int W2 = N == 1024 ? WideShape<1024>::R2 : WideShape<512>::R2;
+  const int passes[2][2] = {{R0, W1}, {R0 * W1, W2}};  // (Ls, r) of passes 2 and 3
   for (int p = 0; p < 2; ++p) {
     const int Ls = passes[p][0], r = passes[p][1];
     for (int q = 0; q < r; ++q)
@@ -128,6 +133,7 @@ struct csl_plan {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   int graph_state = 0;  // 0 not built, 1 ready, -1 failed (host-driven loop)
+  char config[512] = "";
 };
 
 namespace {
@@ -168,12 +174,12 @@ cudaError_t set_attrs_once() {
 // shared memory fits ~100 KB (two or more CTAs per SM).
 template <typename T>
 void choose_cta(PassCfg& c, int want_threads) {
-  const int tpl = pass_tpl(c.N);
+  const int tpl = pass_tpl(c.N, c.wide);
   int threads = want_threads;
-  while (threads > 32 && threads > tpl && pass_smem<T>(c.N, threads / tpl) > 100 * 1024) threads >>= 1;
+  while (threads > 32 && threads > tpl && pass_smem<T>(c.N, c.wide, threads / tpl) > 100 * 1024) threads >>= 1;
   c.lines = threads / tpl;
   c.L.threads = threads;
-  c.L.smem = pass_smem<T>(c.N, c.lines);
+  c.L.smem = pass_smem<T>(c.N, c.wide, c.lines);
 }
 
 template <typename T>
@@ -183,7 +189,7 @@ void config_row(PassCfg& c, int n, int nrows) {
   c.nouter = nrows;
   c.ncols = n;
   int threads = 256;
-  const int tpl = pass_tpl(c.N);
+  const int tpl = pass_tpl(c.N, c.wide);
   // few rows: smaller CTAs so that every SM gets work
   while (threads > 32 && threads / tpl > 1 && (nrows + threads / tpl - 1) / (threads / tpl) < 2 * kSMs) threads >>= 1;
   choose_cta<T>(c, threads);
@@ -199,7 +205,7 @@ void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride,
   c.nouter = nouter;
   c.outer_stride = outer_stride;
   c.line_stride = line_stride;
-  const int tpl = pass_tpl(c.N);
+  const int tpl = pass_tpl(c.N, c.wide);
   int threads = 256;
   if (want_lines > 0) {
     int l = 1;
@@ -227,7 +233,7 @@ RowArgs<T> row_args(csl_plan* P) {
   a.nrows = P->row.nouter;
   a.tw = (const typename C2<T>::t*)P->tw[0];
   a.hs = (const T*)P->hs[0];
-  a.tp = (const typename C2<T>::t*)P->tp[0];
+  a.tp = (const typename C2<T>::t*)P->tp[0] + (P->row.wide ? line_tp_size(P->row.N, false) : 0);
   return a;
 }
 
@@ -242,7 +248,7 @@ StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
   a.line_stride = c.line_stride;
   a.tw = (const typename C2<T>::t*)P->tw[axis];
   a.hs = (const T*)P->hs[axis];
-  a.tp = (const typename C2<T>::t*)P->tp[axis];
+  a.tp = (const typename C2<T>::t*)P->tp[axis] + (c.wide ? line_tp_size(c.N, false) : 0);
   a.data = (typename C2<T>::t*)P->T;
   return a;
 }
@@ -264,7 +270,7 @@ void fill_mid(csl_plan* P, StridedArgs<T>& a, int axis) {
 
 template <typename T>
 cudaError_t run_row(csl_plan* P, int load, int store, const RowArgs<T>& a, cudaStream_t s) {
-  return launch_row<T>(P->row.N, load, store, a, P->row.L, s);
+  return launch_row<T>(P->row.N, P->row.wide, load, store, a, P->row.L, s);
 }
 
 // P^{-1} applied to the plan's T buffer after the x pass: [y fwd,] mid, [y inv]
@@ -276,19 +282,19 @@ cudaError_t launch_mid_chain(csl_plan* P, cudaStream_t s, DevState* st, int scal
     fill_mid<T>(P, m, 1);
     m.st = st;
     m.scalar_mode = scalar_mode;
-    return launch_strided<T>(P->sy.N, true, m, P->sy.L, s);
+    return launch_strided<T>(P->sy.N, P->sy.wide, true, m, P->sy.L, s);
   }
   StridedArgs<T> y = strided_args<T>(P, P->sy, 1);
   y.st = st;
-  e = launch_strided<T>(P->sy.N, false, y, P->sy.L, s);
+  e = launch_strided<T>(P->sy.N, P->sy.wide, false, y, P->sy.L, s);
   if (e != cudaSuccess) return e;
   StridedArgs<T> m = strided_args<T>(P, P->sz, 2);
   fill_mid<T>(P, m, 2);
   m.st = st;
   m.scalar_mode = scalar_mode;
-  e = launch_strided<T>(P->sz.N, true, m, P->sz.L, s);
+  e = launch_strided<T>(P->sz.N, P->sz.wide, true, m, P->sz.L, s);
   if (e != cudaSuccess) return e;
-  return launch_strided<T>(P->sy.N, false, y, P->sy.L, s);
+  return launch_strided<T>(P->sy.N, P->sy.wide, false, y, P->sy.L, s);
 }
 
 template <typename T>
@@ -409,6 +415,138 @@ cudaError_t launch_precondition_T(csl_plan* P, const double2* v, double2* out, c
   r3.tin = (const typename C2<T>::t*)P->T;
   r3.dout = out;
   if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_D, r3, s);
+  return e;
+}
+
+// ---- autotuner ---------------------------------------------------------------
+// Each sine-transform pass is timed (CUDA events on the plan's stream, the
+// plan's own buffers, a scratch solver state) for every CTA size and, for
+// N = 512 and 1024, both transform variants; the fastest is kept.  Results are
+// cached per (precision, pass, geometry) for the life of the process.
+struct TuneKey {
+  int prec, kind, N, ncols, nouter;
+  bool operator<(const TuneKey& o) const {
+    if (prec != o.prec) return prec < o.prec;
+    if (kind != o.kind) return kind < o.kind;
+    if (N != o.N) return N < o.N;
+    if (ncols != o.ncols) return ncols < o.ncols;
+    return nouter < o.nouter;
+  }
+};
+std::map<TuneKey, PassCfg> g_tune_cache;
+std::mutex g_tune_mu;
+
+// launch the pass `kind` once with configuration c: 0 = row pass (P1 + P3 of
+// an iteration), 1 = strided plain, 2 = strided mid
+template <typename T>
+cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
+  if (kind == 0) {
+    const PassCfg keep = P->row;
+    P->row = c;
+    cudaError_t e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, 0), P->stream);
+    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, 0), P->stream);
+    P->row = keep;
+    return e;
+  }
+  StridedArgs<T> a = strided_args<T>(P, c, axis);
+  a.st = P->st;
+  if (kind == 2) {
+    fill_mid<T>(P, a, axis);
+    a.scalar_mode = 2;
+  }
+  return launch_strided<T>(c.N, c.wide, kind == 2, a, c.L, P->stream);
+}
+
+template <typename T>
+cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e0, cudaEvent_t e1,
+                      const DevState& hst) {
+  const TuneKey key = {(int)sizeof(T), kind, c.N, c.ncols, c.nouter};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c = it->second;
+      return cudaSuccess;
+    }
+  }
+  PassCfg best = c;
+  float best_ms = 1e30f;
+  for (int w = 0; w < (pass_has_wide(c.N) ? 2 : 1); ++w) {
+    const int tpl = pass_tpl(c.N, w == 1);
+    for (int lines = 1; lines * tpl <= 256; lines <<= 1) {
+      if (lines * tpl < 32) continue;
+      PassCfg cand = c;
+      cand.wide = (w == 1);
+      cand.lines = lines;
+      cand.L.threads = lines * tpl;
+      cand.L.smem = pass_smem<T>(c.N, cand.wide, lines);
+      if (cand.L.smem > 200 * 1024) continue;
+      long tiles;
+      if (kind == 0) {
+        tiles = (c.nouter + lines - 1) / lines;
+        cand.L.blocks = (int)(tiles < (long)kSMs * 16 ? tiles : (long)kSMs * 16);
+      } else {
+        if (lines > 2 * c.ncols) continue;
+        tiles = (long)((c.ncols + lines - 1) / lines) * c.nouter;
+        cand.L.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
+      }
+      float tot = 0.f;
+      cudaError_t e = cudaSuccess;
+      for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+        e = cudaMemcpyAsync(P->st, &hst, sizeof(hst), cudaMemcpyHostToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+        if (e == cudaSuccess) e = tune_launch<T>(P, kind, cand, axis);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) tot += t;  // the first launch warms up
+      }
+      if (e != cudaSuccess) return e;
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = cand;
+      }
+    }
+  }
+  c = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t autotune(csl_plan* P) {
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.gam = h.gam_old = h.gam1 = 1.0;
+  h.c = h.c_old = 1.0;
+  h.eta = h.eta_x = h.bnorm = 1.0;
+  h.tol = 1e-300;
+  h.maxit = 1 << 30;
+  h.beta = P->beta;
+  DevState* keep = P->st;
+  P->st = P->st_prof;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // the vectors are uninitialised here: give the row pass finite inputs
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(P->v[i], 0, sizeof(double2) * P->M, P->stream);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(P->w[i], 0, sizeof(double2) * P->M, P->stream);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(P->z[i], 0, sizeof(typename C2<T>::t) * P->M, P->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->x, 0, sizeof(double2) * P->M, P->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->T, 0, sizeof(typename C2<T>::t) * P->M, P->stream);
+  if (e == cudaSuccess) e = tune_pass<T>(P, P->row, 0, 0, e0, e1, h);
+  if (P->dim == 2) {
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 2, 1, e0, e1, h);
+  } else {
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 1, 1, e0, e1, h);
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sz, 2, 2, e0, e1, h);
+  }
+  P->st = keep;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   return e;
 }
 
@@ -535,6 +673,7 @@ csl_status csl_plan_options_init(csl_plan_options* opt) {
   opt->gamma_override = kNaN;
   opt->lines_per_cta = 0;
   opt->use_graph = 1;
+  opt->autotune = 1;
   return CSL_OK;
 }
 
@@ -588,7 +727,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     P->mu_f[d] = (float*)dalloc(P, (size_t)P->n[d] * 4, &err);
     P->tw[d] = dalloc(P, (size_t)(N / 2) * 2 * tsz, &err);
     P->hs[d] = dalloc(P, (size_t)(N / 2 + 1) * tsz, &err);
-    P->tp[d] = dalloc(P, (size_t)(line_tp_size(N) + 1) * 2 * tsz, &err);
+    P->tp[d] = dalloc(P, (size_t)(line_tp_size(N, false) + line_tp_size(N, true) + 1) * 2 * tsz, &err);
   }
   P->b = (double2*)dalloc(P, M * 16, &err);
   P->x = (double2*)dalloc(P, M * 16, &err);
@@ -762,9 +901,33 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       config_strided<double>(P->sz, nz, nx, ny, nx, (long)nx * ny, o.lines_per_cta);
     }
   }
+  if (o.autotune && o.lines_per_cta <= 0) {
+    // (the chosen shapes are described in P->config below)
+    err = o.precision == CSL_PREC_FP32 ? autotune<float>(P) : autotune<double>(P);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+      CSL_NOTE(err, "autotune");
+      (void)cudaGetLastError();
+      free_plan(P);
+      return CSL_CUDA_ERROR;
+    }
+  }
+  {
+    const PassCfg* cs[3] = {&P->row, &P->sy, &P->sz};
+    const char* nm[3] = {"x", "y", "z"};
+    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[blocks=%d]",
+                       o.precision == CSL_PREC_FP32 ? "fp32" : "fp64", o.autotune ? " autotuned" : "",
+                       P->sten_blocks);
+    for (int d = 0; d < dim && off < (int)sizeof(P->config); ++d)
+      off += snprintf(P->config + off, sizeof(P->config) - off, " %s[N=%d %s lines=%d threads=%d blocks=%d smem=%zu]",
+                      nm[d], cs[d]->N, cs[d]->wide ? "stockham64" : "warp", cs[d]->lines, cs[d]->L.threads,
+                      cs[d]->L.blocks, cs[d]->L.smem);
+  }
   *out = P;
   return CSL_OK;
 }
+
+const char* csl_plan_config(const csl_plan* plan) { return plan ? plan->config : ""; }
 
 void csl_plan_destroy(csl_plan* plan) {
   if (!plan) return;
@@ -910,7 +1073,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
             fill_mid<float>(P, a, axis);
             a.scalar_mode = 2;
           }
-          err = launch_strided<float>(c.N, mid, a, c.L, P->stream);
+          err = launch_strided<float>(c.N, c.wide, mid, a, c.L, P->stream);
         } else {
           StridedArgs<double> a = strided_args<double>(P, c, axis);
           a.st = P->st;
@@ -918,7 +1081,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
             fill_mid<double>(P, a, axis);
             a.scalar_mode = 2;
           }
-          err = launch_strided<double>(c.N, mid, a, c.L, P->stream);
+          err = launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
         }
       }
       if (err == cudaSuccess) err = cudaEventRecord(e1, P->stream);

@@ -446,8 +446,8 @@ struct LineDst<T, N, true> {
 };
 
 // Host-side size of the extra twiddle table of length N (matches LineDst::TP).
-__host__ __device__ constexpr int line_tp_size(int N) {
-  return N >= 1024 ? wide_tp_size<1024>() : N >= 512 ? wide_tp_size<512>() : N >= 64 ? N : 0;
+__host__ __device__ constexpr int line_tp_size(int N, bool wide) {
+  return wide ? (N >= 1024 ? wide_tp_size<1024>() : N >= 512 ? wide_tp_size<512>() : 0) : (N >= 64 ? N : 0);
 }
 
 // Copy the transform tables of length N into shared memory (block-wide).

@@ -6,44 +6,58 @@
 
 namespace csl {
 
-template <typename T, int N>
+template <typename T, int N, bool W>
 cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
   if (load == LOAD_V && store == STORE_T)
-    k_row<T, N, LOAD_V, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_V, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
   else if (load == LOAD_LANCZOS && store == STORE_T)
-    k_row<T, N, LOAD_LANCZOS, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_LANCZOS, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
   else if (load == LOAD_T && store == STORE_Z)
-    k_row<T, N, LOAD_T, STORE_Z><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_Z><<<L.blocks, L.threads, L.smem, s>>>(a);
   else if (load == LOAD_T && store == STORE_Z_UPDATE)
-    k_row<T, N, LOAD_T, STORE_Z_UPDATE><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_Z_UPDATE><<<L.blocks, L.threads, L.smem, s>>>(a);
   else if (load == LOAD_T && store == STORE_D)
-    k_row<T, N, LOAD_T, STORE_D><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_D><<<L.blocks, L.threads, L.smem, s>>>(a);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_row(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
+                       cudaStream_t s) {
   switch (N) {
-#define CASE(NN) \
-  case NN: return launch_row_n<T, NN>(load, store, a, L, s);
+#define CASE(NN)                                                  \
+  case NN:                                                        \
+    if constexpr (NN >= 512) {                                    \
+      if (wide) return launch_row_n<T, NN, true>(load, store, a, L, s); \
+    }                                                             \
+    return launch_row_n<T, NN, false>(load, store, a, L, s);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
   return cudaErrorInvalidValue;
 }
 
+template <typename T, int N, bool W>
+cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+  if (mid)
+    k_strided<T, N, W, true><<<L.blocks, L.threads, L.smem, s>>>(a);
+  else
+    k_strided<T, N, W, false><<<L.blocks, L.threads, L.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T>
-cudaError_t launch_strided(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
+                           cudaStream_t s) {
   switch (N) {
-#define CASE(NN)                                                          \
-  case NN:                                                                \
-    if (mid)                                                              \
-      k_strided<T, NN, true><<<L.blocks, L.threads, L.smem, s>>>(a);      \
-    else                                                                  \
-      k_strided<T, NN, false><<<L.blocks, L.threads, L.smem, s>>>(a);     \
-    return cudaGetLastError();
+#define CASE(NN)                                                  \
+  case NN:                                                        \
+    if constexpr (NN >= 512) {                                    \
+      if (wide) return launch_strided_n<T, NN, true>(mid, a, L, s); \
+    }                                                             \
+    return launch_strided_n<T, NN, false>(mid, a, L, s);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -67,22 +81,27 @@ cudaError_t set_pass_attrs() {
   cudaError_t e = cudaSuccess;
 #define SETA(k) \
   if (e == cudaSuccess) e = allow_dyn_smem((const void*)k);
-#define CASE(NN)                                    \
-  SETA((k_row<T, NN, LOAD_V, STORE_T>))             \
-  SETA((k_row<T, NN, LOAD_LANCZOS, STORE_T>))       \
-  SETA((k_row<T, NN, LOAD_T, STORE_Z>))             \
-  SETA((k_row<T, NN, LOAD_T, STORE_Z_UPDATE>))      \
-  SETA((k_row<T, NN, LOAD_T, STORE_D>))             \
-  SETA((k_strided<T, NN, true>))                    \
-  SETA((k_strided<T, NN, false>))
+#define VARIANT(NN, W)                                 \
+  SETA((k_row<T, NN, W, LOAD_V, STORE_T>))             \
+  SETA((k_row<T, NN, W, LOAD_LANCZOS, STORE_T>))       \
+  SETA((k_row<T, NN, W, LOAD_T, STORE_Z>))             \
+  SETA((k_row<T, NN, W, LOAD_T, STORE_Z_UPDATE>))      \
+  SETA((k_row<T, NN, W, LOAD_T, STORE_D>))             \
+  SETA((k_strided<T, NN, W, true>))                    \
+  SETA((k_strided<T, NN, W, false>))
+#define CASE(NN) VARIANT(NN, false)
   CSL_FOR_EACH_N(CASE)
 #undef CASE
+  VARIANT(512, true)
+  VARIANT(1024, true)
+#undef VARIANT
 #undef SETA
   return e;
 }
 
-template cudaError_t launch_row<CSL_T>(int, int, int, const RowArgs<CSL_T>&, const PassLaunch&, cudaStream_t);
-template cudaError_t launch_strided<CSL_T>(int, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
+template cudaError_t launch_row<CSL_T>(int, bool, int, int, const RowArgs<CSL_T>&, const PassLaunch&,
+                                       cudaStream_t);
+template cudaError_t launch_strided<CSL_T>(int, bool, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
                                            cudaStream_t);
 template cudaError_t set_pass_attrs<CSL_T>();
 

@@ -62,24 +62,24 @@ struct StridedArgs {
 
 // byte offsets of the shared-memory regions: twiddles | half sines | extra
 // twiddles | scan scratch (2 per line) | lines
-template <typename T, int N>
+template <typename T, int N, bool WIDE>
 __host__ __device__ constexpr size_t pass_tables_bytes() {
   return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16 +
-         (size_t)line_tp_size(N) * sizeof(typename C2<T>::t);
+         (size_t)line_tp_size(N, WIDE) * sizeof(typename C2<T>::t);
 }
-template <typename T, int N>
+template <typename T, int N, bool WIDE>
 __host__ __device__ constexpr size_t pass_smem_bytes(int lines) {
-  return pass_tables_bytes<T, N>() + (size_t)lines * 2 * sizeof(typename C2<T>::t) +
-         (size_t)lines * LineDst<T, N>::LS * sizeof(typename C2<T>::t);
+  return pass_tables_bytes<T, N, WIDE>() + (size_t)lines * 2 * sizeof(typename C2<T>::t) +
+         (size_t)lines * LineDst<T, N, WIDE>::LS * sizeof(typename C2<T>::t);
 }
 
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
-template <typename T, int N, int LOAD, int STORE>
+template <typename T, int N, bool WIDE, int LOAD, int STORE>
 __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
   typedef typename C2<T>::t c_t;
-  typedef LineDst<T, N> D;
+  typedef LineDst<T, N, WIDE> D;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
   constexpr int UB = NL < 8 ? NL : 8;      // load batch
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
   T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
   c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
   const int nlines = blockDim.x / TPL;
-  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
   c_t* lines = s_scr + 2 * nlines;
   load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
@@ -203,10 +203,10 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
   }
 }
 
-template <typename T, int N, bool MID>
+template <typename T, int N, bool WIDE, bool MID>
 __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
   typedef typename C2<T>::t c_t;
-  typedef LineDst<T, N> D;
+  typedef LineDst<T, N, WIDE> D;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;
   constexpr int UB = NL < 8 ? NL : 8;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
   T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
   c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
   const int C = blockDim.x / TPL;  // lines (columns) per tile, a power of two
-  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N>());
+  c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
   c_t* lines = s_scr + 2 * C;
   load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   int logC = 0;
@@ -319,21 +319,37 @@ struct PassLaunch {
 
 #define CSL_FOR_EACH_N(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
+// N = 512 and 1024 exist in both variants (warp-per-line four-step and the
+// two-warp Stockham path); the autotuner picks one per pass.
+inline bool pass_has_wide(int N) { return N == 512 || N == 1024; }
+
 template <typename T>
-size_t pass_smem(int N, int lines) {
+size_t pass_smem(int N, bool wide, int lines) {
   switch (N) {
-#define CASE(NN) \
-  case NN: return pass_smem_bytes<T, NN>(lines);
+#define CASE(NN)                                                                       \
+  case NN:                                                                             \
+    if constexpr (NN >= 512) {                                                         \
+      if (wide) return pass_smem_bytes<T, NN, true>(lines);                            \
+    }                                                                                  \
+    return pass_smem_bytes<T, NN, false>(lines);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
   return 0;
 }
 
-inline int pass_tpl(int N) {
+template <int NN>
+inline int pass_tpl_n(bool wide) {
+  if constexpr (NN >= 512) {
+    if (wide) return LineDst<float, NN, true>::TPL;
+  }
+  return LineDst<float, NN, false>::TPL;
+}
+
+inline int pass_tpl(int N, bool wide) {
   switch (N) {
 #define CASE(NN) \
-  case NN: return LineDst<float, NN>::TPL;
+  case NN: return pass_tpl_n<NN>(wide);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -341,9 +357,11 @@ inline int pass_tpl(int N) {
 }
 
 template <typename T>
-cudaError_t launch_row(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s);
+cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
+                       cudaStream_t s);
 template <typename T>
-cudaError_t launch_strided(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s);
+cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
+                           cudaStream_t s);
 template <typename T>
 cudaError_t set_pass_attrs();
 

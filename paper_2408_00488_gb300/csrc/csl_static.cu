@@ -166,15 +166,16 @@ void setup_device(int dev) {
 // CTA shape of one pass (same rules as the plan's default configuration)
 template <typename T>
 PassLaunch static_launch(int N, long nlines_or_tiles_per_cta_unit, bool strided, int ncols, int nouter) {
-  const int tpl = pass_tpl(N);
+  const bool wide = pass_has_wide(N);
+  const int tpl = pass_tpl(N, wide);
   int threads = 256;
   if (strided)
     while (threads > 32 && threads > tpl && (threads / tpl) / 2 >= ncols) threads >>= 1;
-  while (threads > 32 && threads > tpl && pass_smem<T>(N, threads / tpl) > 100 * 1024) threads >>= 1;
+  while (threads > 32 && threads > tpl && pass_smem<T>(N, wide, threads / tpl) > 100 * 1024) threads >>= 1;
   const int lines = threads / tpl;
   PassLaunch L;
   L.threads = threads;
-  L.smem = pass_smem<T>(N, lines);
+  L.smem = pass_smem<T>(N, wide, lines);
   long tiles = strided ? (long)((ncols + lines - 1) / lines) * nouter : (nlines_or_tiles_per_cta_unit + lines - 1) / lines;
   L.blocks = (int)(tiles < 4096 ? tiles : 4096);
   return L;
@@ -214,7 +215,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
   r1.vin = v;
   r1.tout = Tbuf;
   const PassLaunch Lr = static_launch<T>(nx + 1, M / nx, false, 0, 0);
-  e = launch_row<T>(nx + 1, LOAD_V, STORE_T, r1, Lr, s);
+  e = launch_row<T>(nx + 1, pass_has_wide(nx + 1), LOAD_V, STORE_T, r1, Lr, s);
   if (e != cudaSuccess) return e;
   auto strided = [&](int axis, int nn, int nouter, long outer_stride, long line_stride, bool mid) {
     StridedArgs<T> a;
@@ -242,7 +243,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
       a.cnorm = (T)cnorm;
     }
     const PassLaunch L = static_launch<T>(nn + 1, 0, true, nx, nouter);
-    return launch_strided<T>(nn + 1, mid, a, L, s);
+    return launch_strided<T>(nn + 1, pass_has_wide(nn + 1), mid, a, L, s);
   };
   if (dim == 2) {
     e = strided(1, ny, 1, 0, nx, true);
@@ -257,7 +258,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
   r3.tout = nullptr;
   r3.tin = Tbuf;
   r3.dout = out;
-  return launch_row<T>(nx + 1, LOAD_T, STORE_D, r3, Lr, s);
+  return launch_row<T>(nx + 1, pass_has_wide(nx + 1), LOAD_T, STORE_D, r3, Lr, s);
 }
 
 }  // namespace

@@ -50,7 +50,7 @@ def test_options_init(csl):
     b = csl._binding
     o = b.PlanOptions()
     assert csl.lib.csl_plan_options_init(ctypes.byref(o)) == 0
-    assert o.precision == 0 and o.use_graph == 1 and o.lines_per_cta == 0
+    assert o.precision == 0 and o.use_graph == 1 and o.lines_per_cta == 0 and o.autotune == 1
     assert o.gamma_override != o.gamma_override  # NaN: derive gamma from the samples
     assert csl.lib.csl_plan_options_init(None) == b.INVALID_ARG
 
@@ -80,4 +80,5 @@ def test_host_side_argument_validation(csl):
     assert csl.lib.csl_precondition(None, None, None) == b.INVALID_ARG
     assert csl.lib.csl_coef_grad(None, None, None, None) == b.INVALID_ARG
     assert csl.lib.csl_plan_workspace_bytes(None) == 0
+    assert csl.lib.csl_plan_config(None) == b""
     csl.lib.csl_plan_destroy(None)
