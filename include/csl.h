@@ -182,6 +182,38 @@ csl_status csl_coef_grad(csl_plan* plan, const double* z, const double* y,
                          double* const grad_faces[3]);
 
 /*
+ * Batched solves (many shifts lambda_k, e.g. from an alpha-circulant time
+ * discretisation, and grids of different sizes): one plan per system, all
+ * systems of one grid size advanced together by the same kernels (a device
+ * array of per-system arguments per launch), the size groups on parallel
+ * branches of one CUDA graph whose WHILE node is closed once every system
+ * has met its own stopping test.  Converged systems stop costing work.
+ */
+typedef struct csl_system_desc {
+  int dim;                           /* 2 or 3 (the same for all systems of a batch) */
+  int64_t n[3];                      /* grid, as for csl_plan_create                 */
+  const double* coef_faces[3];       /* device pointers, as for csl_plan_create       */
+  double alpha, beta;                /* lambda = alpha + i beta                        */
+} csl_system_desc;
+
+typedef struct csl_batch csl_batch;
+
+/* Build a batch of nsys systems (opt applies to all; opt may be NULL). */
+csl_status csl_batch_create(csl_batch** out, int nsys, const csl_system_desc* sys,
+                            const csl_plan_options* opt, void* stream);
+
+/*
+ * Solve every system: f[i], z[i] are device complex128 pointers (host arrays
+ * of nsys pointers).  infos (nsys entries) may be NULL.  Returns CSL_OK if
+ * every system converged, else the first non-OK system status.  Synchronises
+ * the batch's stream.
+ */
+csl_status csl_batch_solve(csl_batch* batch, const double* const* f, double* const* z, double tol, int maxit,
+                           csl_solve_info* infos);
+void csl_batch_destroy(csl_batch* batch);
+size_t csl_batch_workspace_bytes(const csl_batch* batch);
+
+/*
  * Allocation-free P^{-1} v (the paper has no counterpart; a deployment
  * convenience).  Same result as csl_precondition on a plan built with the
  * same grid, gamma, alpha, beta and precision, but without a plan and without

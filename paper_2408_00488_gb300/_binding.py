@@ -29,6 +29,11 @@ class SolveInfo(ctypes.Structure):
                 ("launches", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
+class SystemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("coef_faces", ctypes.c_void_p * 3),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _SIGS = {
@@ -52,6 +57,12 @@ _SIGS = {
     "csl_coef_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
     "csl_precondition_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+    "csl_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SystemDesc),
+                                        ctypes.POINTER(PlanOptions), _P]),
+    "csl_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(SolveInfo)]),
+    "csl_batch_destroy": (None, [_P]),
+    "csl_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
     "csl_time_kernels": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]),
 }
@@ -284,6 +295,67 @@ class Plan:
         _check(lib.csl_coef_grad(self._h, _dptr(z, ("complex128",), "z"), _dptr(y, ("complex128",), "y"),
                                  ptrs), "csl_coef_grad")
         return tuple(grads)
+
+
+class Batch:
+    """Many systems solved together (csl_batch_*): systems is a list of
+    (faces, lam) with faces as for Plan; all systems share dim and precision."""
+
+    def __init__(self, systems, precision: str = "fp64", autotune: bool = True, stream=None):
+        self.n = len(systems)
+        descs = (SystemDesc * self.n)()
+        self._keep = []
+        self.shapes = []
+        for i, (faces, lam) in enumerate(systems):
+            faces = [f.contiguous() for f in faces]
+            self._keep.append(faces)
+            dim = len(faces)
+            nx = faces[0].shape[-1] - 1
+            ny = faces[0].shape[-2]
+            nz = faces[0].shape[-3] if dim == 3 else 1
+            self.shapes.append((ny, nx) if dim == 2 else (nz, ny, nx))
+            descs[i].dim = dim
+            descs[i].n[0], descs[i].n[1], descs[i].n[2] = nx, ny, nz
+            for d in range(3):
+                descs[i].coef_faces[d] = _dptr(faces[d], ("float64",), "faces") if d < dim else None
+            lam = complex(lam)
+            descs[i].alpha, descs[i].beta = lam.real, lam.imag
+        opt = PlanOptions()
+        lib.csl_plan_options_init(ctypes.byref(opt))
+        opt.precision = _PREC[precision]
+        opt.autotune = 1 if autotune else 0
+        h = _P()
+        _check(lib.csl_batch_create(ctypes.byref(h), self.n, descs, ctypes.byref(opt), _stream_handle(stream)),
+               "csl_batch_create")
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.csl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, fs, tol: float = 1e-8, maxit: int = 1000, outs=None):
+        torch = _torch()
+        zs = [torch.empty_like(f) for f in fs] if outs is None else outs
+        fp = (_P * self.n)(*[_dptr(f, ("complex128",), "f") for f in fs])
+        zp = (_P * self.n)(*[_dptr(z, ("complex128",), "z") for z in zs])
+        infos = (SolveInfo * self.n)()
+        st = lib.csl_batch_solve(self._h, fp, zp, float(tol), int(maxit), infos)
+        _check(st, "csl_batch_solve", allow=(OK, NOT_CONVERGED, BREAKDOWN))
+        return zs, [Info.from_c(infos[i]) for i in range(self.n)]
 
 
 def precondition_static(v, gamma: float, lam: complex, precision: str = "fp64", out=None, stream=None):

@@ -319,9 +319,9 @@ cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) 
   a.use_cond = use_cond ? 1 : 0;
   typedef typename C2<T>::t TZ;
   if (P->dim == 2)
-    k_stencil<2, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
+    k_stencil<2, TZ><<<P->sten_blocks, 256, 0, s>>>(a, nullptr, 0);
   else
-    k_stencil<3, TZ><<<P->sten_blocks, 256, 0, s>>>(a);
+    k_stencil<3, TZ><<<P->sten_blocks, 256, 0, s>>>(a, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -383,7 +383,7 @@ cudaError_t launch_prologue_T(csl_plan* P, const double2* f, double tol, int max
   ia.maxit = maxit;
   ia.sqrt_pmin = P->sqrt_pmin;
   ia.sqrt_pmax = P->sqrt_pmax;
-  k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia);
+  k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   RowArgs<T> r1 = row_args<T>(P);
   r1.vin = P->v[0];
@@ -1103,6 +1103,483 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
     return CSL_CUDA_ERROR;
   }
   return CSL_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batched solves: many independent systems (shifts lambda_k, and grids of
+// different sizes) in one graph launch.  Systems of the same grid form a group;
+// each kernel of an iteration is launched once per group with a device array
+// of per-system arguments (system = blockIdx / blocks-per-system), so a group
+// of small grids fills the GPU.  Groups run on parallel branches of the
+// graph; a one-CTA control kernel closes the WHILE node once every system has
+// met its stopping test (or an integer iteration cap is reached).  Converged
+// systems' CTAs exit at entry.
+// ============================================================================
+namespace {
+
+struct BatchGroup {
+  int n[3] = {1, 1, 1};
+  std::vector<int> sys;  // indices of the group's systems
+  csl_plan* proto = nullptr;
+  StencilArgs* d_sten[2] = {nullptr, nullptr};
+  void* d_p1[2] = {nullptr, nullptr};   // RowArgs<T>
+  void* d_p3[2] = {nullptr, nullptr};   // RowArgs<T>
+  void* d_mid = nullptr;                // StridedArgs<T> (mid pass, iteration)
+  void* d_y = nullptr;                  // StridedArgs<T> (3D y pass)
+  IngestArgs* d_ing = nullptr;
+  void* d_pro1 = nullptr;               // RowArgs<T> prologue x-fwd
+  void* d_pro_mid = nullptr;            // StridedArgs<T> prologue mid (scalar mode 1)
+  void* d_pro3 = nullptr;               // RowArgs<T> prologue x-inv -> z[0]
+  std::vector<IngestArgs> h_ing;
+  cudaStream_t branch = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+
+// loops[0]: WHILE bodies run so far; loops[1]: cap on them (set per solve)
+__global__ void k_batch_control(DevState* states, int nsys, int* loops, cudaGraphConditionalHandle cond) {
+  __shared__ int remaining;
+  if (threadIdx.x == 0) remaining = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) mine += states[s].done ? 0 : 1;
+  atomicAdd(&remaining, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int l = ++loops[0];
+    cudaGraphSetConditional(cond, (remaining > 0 && l <= loops[1]) ? 1u : 0u);
+  }
+}
+
+__global__ void k_batch_copy(const double2* const* src, double2* const* dst, const long* count) {
+  const int s = blockIdx.y;
+  const double2* a = src[s];
+  double2* b = dst[s];
+  const long M = count[s];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (long)gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+}  // namespace
+
+struct csl_batch {
+  int nsys = 0, precision = CSL_PREC_FP64, dim = 2;
+  std::vector<csl_plan*> plans;
+  std::vector<BatchGroup> groups;
+  DevState* states = nullptr;
+  int* d_loops = nullptr;
+  int h_loops[2] = {0, 0};
+  const double2** d_src = nullptr;
+  double2** d_dst = nullptr;
+  long* d_count = nullptr;
+  long maxM = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int graph_state = 0;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+namespace {
+
+cudaError_t balloc(csl_batch* B, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    B->allocs.push_back(*p);
+    B->bytes += bytes;
+  }
+  return e;
+}
+
+template <typename A>
+cudaError_t upload_array(csl_batch* B, void** d, const std::vector<A>& h) {
+  cudaError_t e = balloc(B, d, sizeof(A) * h.size());
+  if (e == cudaSuccess) e = cudaMemcpy(*d, h.data(), sizeof(A) * h.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_batch(csl_batch* B) {
+  if (!B) return;
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto& g : B->groups) {
+    if (g.branch) cudaStreamDestroy(g.branch);
+    if (g.ev) cudaEventDestroy(g.ev);
+  }
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  for (void* p : B->allocs) cudaFree(p);
+  for (csl_plan* P : B->plans) free_plan(P);
+  delete B;
+}
+
+// per-system argument arrays of one group
+template <typename T>
+cudaError_t build_group_args(csl_batch* B, BatchGroup& G) {
+  const int ns = (int)G.sys.size();
+  cudaError_t e = cudaSuccess;
+  for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+    std::vector<StencilArgs> sa(ns);
+    std::vector<RowArgs<T>> p1(ns), p3(ns);
+    for (int i = 0; i < ns; ++i) {
+      csl_plan* P = B->plans[G.sys[i]];
+      StencilArgs a;
+      memset(&a, 0, sizeof(a));
+      a.g.nx = P->n[0];
+      a.g.ny = P->n[1];
+      a.g.nz = P->dim == 3 ? P->n[2] : 1;
+      a.g.M = P->M;
+      a.z = P->z[par];
+      a.vold = P->v[1 - par];
+      a.cx = P->cx;
+      a.cy = P->cy;
+      a.cz = P->cz;
+      a.dg = P->dg;
+      a.x = P->x;
+      a.b = P->b;
+      a.st = P->st;
+      a.partials = P->partials;
+      a.use_cond = 0;
+      sa[i] = a;
+      p1[i] = p1_args<T>(P, par);
+      p3[i] = p3_args<T>(P, par);
+    }
+    e = upload_array(B, (void**)&G.d_sten[par], sa);
+    if (e == cudaSuccess) e = upload_array(B, &G.d_p1[par], p1);
+    if (e == cudaSuccess) e = upload_array(B, &G.d_p3[par], p3);
+  }
+  std::vector<StridedArgs<T>> mid(ns), y(ns), pmid(ns);
+  std::vector<RowArgs<T>> pro1(ns), pro3(ns);
+  G.h_ing.resize(ns);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+    csl_plan* P = B->plans[G.sys[i]];
+    const int ax = P->dim == 2 ? 1 : 2;
+    const PassCfg& cm = P->dim == 2 ? P->sy : P->sz;
+    StridedArgs<T> m = strided_args<T>(P, cm, ax);
+    fill_mid<T>(P, m, ax);
+    m.st = P->st;
+    m.scalar_mode = 2;
+    mid[i] = m;
+    m.scalar_mode = 1;
+    pmid[i] = m;
+    StridedArgs<T> yy = strided_args<T>(P, P->sy, 1);
+    yy.st = P->st;
+    y[i] = yy;
+    RowArgs<T> r1 = row_args<T>(P);
+    r1.vin = P->v[0];
+    r1.tout = (typename C2<T>::t*)P->T;
+    r1.st = P->st;
+    pro1[i] = r1;
+    RowArgs<T> r3 = row_args<T>(P);
+    r3.tin = (const typename C2<T>::t*)P->T;
+    r3.zout = (typename C2<T>::t*)P->z[0];
+    r3.st = P->st;
+    pro3[i] = r3;
+    IngestArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.M = P->M;
+    ia.b = P->b;
+    ia.v0 = P->v[0];
+    ia.v1 = P->v[1];
+    ia.w0 = P->w[0];
+    ia.w1 = P->w[1];
+    ia.x = P->x;
+    ia.st = P->st;
+    ia.partials = P->partials;
+    ia.sqrt_pmin = P->sqrt_pmin;
+    ia.sqrt_pmax = P->sqrt_pmax;
+    ia.beta = P->beta;
+    G.h_ing[i] = ia;
+  }
+  if (e == cudaSuccess) e = upload_array(B, &G.d_mid, mid);
+  if (e == cudaSuccess) e = upload_array(B, &G.d_y, y);
+  if (e == cudaSuccess) e = upload_array(B, &G.d_pro_mid, pmid);
+  if (e == cudaSuccess) e = upload_array(B, &G.d_pro1, pro1);
+  if (e == cudaSuccess) e = upload_array(B, &G.d_pro3, pro3);
+  if (e == cudaSuccess) e = upload_array(B, (void**)&G.d_ing, G.h_ing);
+  return e;
+}
+
+// P^{-1} chain of a group after the x pass: [y fwd,] mid, [y inv]
+template <typename T>
+cudaError_t group_mid_chain(csl_batch* B, BatchGroup& G, cudaStream_t s, const void* d_mid) {
+  csl_plan* P = G.proto;
+  const int ns = (int)G.sys.size();
+  StridedArgs<T> dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  if (P->dim == 2)
+    return launch_strided<T>(P->sy.N, P->sy.wide, true, dummy, P->sy.L, s, (const StridedArgs<T>*)d_mid, ns);
+  cudaError_t e =
+      launch_strided<T>(P->sy.N, P->sy.wide, false, dummy, P->sy.L, s, (const StridedArgs<T>*)G.d_y, ns);
+  if (e == cudaSuccess)
+    e = launch_strided<T>(P->sz.N, P->sz.wide, true, dummy, P->sz.L, s, (const StridedArgs<T>*)d_mid, ns);
+  if (e == cudaSuccess)
+    e = launch_strided<T>(P->sy.N, P->sy.wide, false, dummy, P->sy.L, s, (const StridedArgs<T>*)G.d_y, ns);
+  return e;
+}
+
+template <typename T>
+cudaError_t group_iteration(csl_batch* B, BatchGroup& G, int par, cudaStream_t s) {
+  csl_plan* P = G.proto;
+  const int ns = (int)G.sys.size();
+  typedef typename C2<T>::t TZ;
+  StencilArgs sd;
+  memset(&sd, 0, sizeof(sd));
+  if (P->dim == 2)
+    k_stencil<2, TZ><<<P->sten_blocks * ns, 256, 0, s>>>(sd, G.d_sten[par], P->sten_blocks);
+  else
+    k_stencil<3, TZ><<<P->sten_blocks * ns, 256, 0, s>>>(sd, G.d_sten[par], P->sten_blocks);
+  cudaError_t e = cudaGetLastError();
+  RowArgs<T> rd;
+  memset(&rd, 0, sizeof(rd));
+  if (e == cudaSuccess)
+    e = launch_row<T>(P->row.N, P->row.wide, LOAD_LANCZOS, STORE_T, rd, P->row.L, s,
+                      (const RowArgs<T>*)G.d_p1[par], ns);
+  if (e == cudaSuccess) e = group_mid_chain<T>(B, G, s, G.d_mid);
+  if (e == cudaSuccess)
+    e = launch_row<T>(P->row.N, P->row.wide, LOAD_T, STORE_Z_UPDATE, rd, P->row.L, s,
+                      (const RowArgs<T>*)G.d_p3[par], ns);
+  return e;
+}
+
+template <typename T>
+cudaError_t group_prologue(csl_batch* B, BatchGroup& G, cudaStream_t s) {
+  csl_plan* P = G.proto;
+  const int ns = (int)G.sys.size();
+  IngestArgs id;
+  memset(&id, 0, sizeof(id));
+  k_ingest<<<P->ew_blocks * ns, 256, 0, s>>>(id, G.d_ing, P->ew_blocks);
+  cudaError_t e = cudaGetLastError();
+  RowArgs<T> rd;
+  memset(&rd, 0, sizeof(rd));
+  if (e == cudaSuccess)
+    e = launch_row<T>(P->row.N, P->row.wide, LOAD_V, STORE_T, rd, P->row.L, s, (const RowArgs<T>*)G.d_pro1, ns);
+  if (e == cudaSuccess) e = group_mid_chain<T>(B, G, s, G.d_pro_mid);
+  if (e == cudaSuccess)
+    e = launch_row<T>(P->row.N, P->row.wide, LOAD_T, STORE_Z, rd, P->row.L, s, (const RowArgs<T>*)G.d_pro3, ns);
+  return e;
+}
+
+template <typename T>
+void build_batch_graph(csl_batch* B) {
+  if (B->graph_state != 0) return;
+  B->graph_state = -1;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&B->cond, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    cp.conditional.handle = B->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaEventRecord(B->ev_fork, B->cap);
+      for (auto& G : B->groups) {
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(G.branch, B->ev_fork, 0);
+        for (int par = 0; par < 2 && e1 == cudaSuccess; ++par) e1 = group_iteration<T>(B, G, par, G.branch);
+        if (e1 == cudaSuccess) e1 = cudaEventRecord(G.ev, G.branch);
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(B->cap, G.ev, 0);
+      }
+      if (e1 == cudaSuccess) {
+        k_batch_control<<<1, 256, 0, B->cap>>>(B->states, B->nsys, B->d_loops, B->cond);
+        e1 = cudaGetLastError();
+      }
+      cudaGraph_t captured = body;
+      e = cudaStreamEndCapture(B->cap, &captured);
+      if (e == cudaSuccess) e = e1;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->gexec, g, 0);
+  if (e != cudaSuccess) {
+    CSL_NOTE(e, "batch graph build");
+    (void)cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    B->gexec = nullptr;
+    return;
+  }
+  B->graph = g;
+  B->graph_state = 1;
+}
+
+template <typename T>
+csl_status batch_solve_T(csl_batch* B, const double* const* f, double* const* z, double tol, int maxit,
+                         csl_solve_info* infos) {
+  cudaStream_t s = B->stream;
+  // per-call inputs: right-hand side pointers and the stopping parameters
+  for (auto& G : B->groups) {
+    for (size_t i = 0; i < G.sys.size(); ++i) {
+      IngestArgs& ia = G.h_ing[i];
+      ia.f = (const double2*)f[G.sys[i]];
+      ia.tol = tol;
+      ia.maxit = maxit;
+    }
+    CSL_TRY(cudaMemcpyAsync(G.d_ing, G.h_ing.data(), sizeof(IngestArgs) * G.h_ing.size(), cudaMemcpyHostToDevice, s));
+    CSL_TRY(group_prologue<T>(B, G, s));
+  }
+  build_batch_graph<T>(B);
+  B->h_loops[0] = 0;
+  B->h_loops[1] = maxit / 2 + 4;
+  CSL_TRY(cudaMemcpyAsync(B->d_loops, B->h_loops, sizeof(B->h_loops), cudaMemcpyHostToDevice, s));
+  if (B->graph_state == 1) {
+    CSL_TRY(cudaGraphLaunch(B->gexec, s));
+  } else {
+    int done = 0;
+    for (int it = 0; it < maxit + 4 && !done; it += 8) {
+      for (int k = 0; k < 8; ++k)
+        for (auto& G : B->groups) CSL_TRY(group_iteration<T>(B, G, k & 1, s));
+      std::vector<DevState> h(B->nsys);
+      CSL_TRY(cudaMemcpyAsync(h.data(), B->states, sizeof(DevState) * B->nsys, cudaMemcpyDeviceToHost, s));
+      CSL_TRY(cudaStreamSynchronize(s));
+      done = 1;
+      for (auto& st : h) done &= st.done;
+    }
+  }
+  // egress: x of every system to its z
+  std::vector<const double2*> src(B->nsys);
+  std::vector<double2*> dst(B->nsys);
+  std::vector<long> cnt(B->nsys);
+  for (int i = 0; i < B->nsys; ++i) {
+    src[i] = B->plans[i]->x;
+    dst[i] = (double2*)z[i];
+    cnt[i] = B->plans[i]->M;
+  }
+  CSL_TRY(cudaMemcpyAsync(B->d_src, src.data(), sizeof(void*) * B->nsys, cudaMemcpyHostToDevice, s));
+  CSL_TRY(cudaMemcpyAsync(B->d_dst, dst.data(), sizeof(void*) * B->nsys, cudaMemcpyHostToDevice, s));
+  CSL_TRY(cudaMemcpyAsync(B->d_count, cnt.data(), sizeof(long) * B->nsys, cudaMemcpyHostToDevice, s));
+  dim3 grid((unsigned)((B->maxM + 255) / 256 < 256 ? (B->maxM + 255) / 256 : 256), (unsigned)B->nsys);
+  k_batch_copy<<<grid, 256, 0, s>>>(B->d_src, B->d_dst, B->d_count);
+  CSL_TRY(cudaGetLastError());
+  std::vector<DevState> h(B->nsys);
+  CSL_TRY(cudaMemcpyAsync(h.data(), B->states, sizeof(DevState) * B->nsys, cudaMemcpyDeviceToHost, s));
+  CSL_TRY(cudaStreamSynchronize(s));
+  csl_status worst = CSL_OK;
+  for (int i = 0; i < B->nsys; ++i) {
+    const csl_status st = h[i].done ? (csl_status)h[i].status : CSL_NOT_CONVERGED;
+    if (st != CSL_OK && worst == CSL_OK) worst = st;
+    if (infos) {
+      memset(&infos[i], 0, sizeof(csl_solve_info));
+      infos[i].iters = h[i].iter;
+      infos[i].status = (int)st;
+      infos[i].relres = h[i].relres;
+      infos[i].pnorm = h[i].eta_x;
+      infos[i].gamma = B->plans[i]->gamma;
+      infos[i].checks = h[i].checks;
+    }
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+csl_status csl_batch_create(csl_batch** out, int nsys, const csl_system_desc* sys, const csl_plan_options* opt,
+                            void* stream) {
+  if (!out || nsys < 1 || !sys) return CSL_INVALID_ARG;
+  *out = nullptr;
+  csl_plan_options o;
+  csl_plan_options_init(&o);
+  if (opt) o = *opt;
+  for (int i = 0; i < nsys; ++i)
+    if (sys[i].dim != sys[0].dim) return CSL_INVALID_ARG;
+  csl_batch* B = new (std::nothrow) csl_batch();
+  if (!B) return CSL_OUT_OF_MEMORY;
+  B->nsys = nsys;
+  B->precision = o.precision;
+  B->dim = sys[0].dim;
+  B->stream = (cudaStream_t)stream;
+  // one plan per system (its workspace and tables); shapes are tuned once per
+  // grid size (the tuner's cache) and shared by the group
+  for (int i = 0; i < nsys; ++i) {
+    csl_plan* P = nullptr;
+    const csl_status st = csl_plan_create(&P, sys[i].dim, sys[i].n, sys[i].coef_faces, sys[i].alpha, sys[i].beta,
+                                          &o, stream);
+    if (st != CSL_OK) {
+      free_batch(B);
+      return st;
+    }
+    B->plans.push_back(P);
+    B->maxM = P->M > B->maxM ? P->M : B->maxM;
+  }
+  cudaError_t e = balloc(B, (void**)&B->states, sizeof(DevState) * nsys);
+  if (e == cudaSuccess) e = cudaMemset(B->states, 0, sizeof(DevState) * nsys);
+  if (e == cudaSuccess) e = balloc(B, (void**)&B->d_loops, 2 * sizeof(int));
+  if (e == cudaSuccess) e = balloc(B, (void**)&B->d_src, sizeof(void*) * nsys);
+  if (e == cudaSuccess) e = balloc(B, (void**)&B->d_dst, sizeof(void*) * nsys);
+  if (e == cudaSuccess) e = balloc(B, (void**)&B->d_count, sizeof(long) * nsys);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+  // the systems' scalar states live side by side so one copy reads them all
+  for (int i = 0; i < nsys; ++i) B->plans[i]->st = B->states + i;
+  // groups: systems with the same grid
+  for (int i = 0; i < nsys && e == cudaSuccess; ++i) {
+    csl_plan* P = B->plans[i];
+    BatchGroup* G = nullptr;
+    for (auto& g : B->groups)
+      if (g.n[0] == P->n[0] && g.n[1] == P->n[1] && g.n[2] == P->n[2]) G = &g;
+    if (!G) {
+      B->groups.emplace_back();
+      G = &B->groups.back();
+      for (int d = 0; d < 3; ++d) G->n[d] = P->n[d];
+      G->proto = P;
+    }
+    G->sys.push_back(i);
+  }
+  for (auto& G : B->groups) {
+    // the group shares its prototype's launch shapes
+    for (int i : G.sys) {
+      csl_plan* P = B->plans[i];
+      P->row = G.proto->row;
+      P->sy = G.proto->sy;
+      P->sz = G.proto->sz;
+      P->sten_blocks = G.proto->sten_blocks;
+      P->ew_blocks = G.proto->ew_blocks;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.branch, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = o.precision == CSL_PREC_FP32 ? build_group_args<float>(B, G) : build_group_args<double>(B, G);
+  }
+  if (e != cudaSuccess) {
+    CSL_NOTE(e, "csl_batch_create");
+    (void)cudaGetLastError();
+    free_batch(B);
+    return e == cudaErrorMemoryAllocation ? CSL_OUT_OF_MEMORY : CSL_CUDA_ERROR;
+  }
+  *out = B;
+  return CSL_OK;
+}
+
+csl_status csl_batch_solve(csl_batch* B, const double* const* f, double* const* z, double tol, int maxit,
+                           csl_solve_info* infos) {
+  if (!B || !f || !z || !(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
+  for (int i = 0; i < B->nsys; ++i)
+    if (!f[i] || !z[i]) return CSL_INVALID_ARG;
+  return B->precision == CSL_PREC_FP32 ? batch_solve_T<float>(B, f, z, tol, maxit, infos)
+                                       : batch_solve_T<double>(B, f, z, tol, maxit, infos);
+}
+
+void csl_batch_destroy(csl_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  free_batch(B);
+}
+
+size_t csl_batch_workspace_bytes(const csl_batch* B) {
+  if (!B) return 0;
+  size_t t = B->bytes;
+  for (csl_plan* P : B->plans) t += P->bytes;
+  return t;
 }
 
 }  // extern "C"

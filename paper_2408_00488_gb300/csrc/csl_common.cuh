@@ -113,18 +113,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*N
 // partials[blockIdx.x*NV + i]; the last block to arrive (atomic ticket) sums
 // the deposits in block order and returns true with the totals in tot[]
 // (valid in all threads of that block).  The ticket is re-armed for reuse.
+// bid / nblk: the block's index and the number of blocks working on the same
+// system (the whole grid for a single system; one slice of a batched launch).
 template <int NV>
 __device__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned int* ticket,
-                                    double (&tot)[NV]) {
+                                    double (&tot)[NV], int bid, int nblk) {
   __shared__ double sh[32 * NV];
   __shared__ int s_last;
   block_sum<NV>(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) partials[blockIdx.x * NV + i] = v[i];
+    for (int i = 0; i < NV; ++i) partials[bid * NV + i] = v[i];
     __threadfence();
     unsigned int t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -132,7 +134,7 @@ __device__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned 
   double acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[b * NV + i];
   }

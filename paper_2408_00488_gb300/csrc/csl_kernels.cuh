@@ -193,12 +193,17 @@ struct StripWindow {
   }
 };
 
+// batch: optional per-system argument array (system = blockIdx.x / bps)
 template <int DIM, typename TZ>
-__global__ void __launch_bounds__(256) k_stencil(StencilArgs a) {
+__global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
+  const int sys = batch ? (int)(blockIdx.x / bps) : 0;
+  const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
+  const int nblk = batch ? bps : (int)gridDim.x;
+  const StencilArgs a = batch ? batch[sys] : a0;
   DevState* st = a.st;
   if (st->done) {
     // keep the device-side loop closed whatever set `done` (Givens breakdown, cap, ...)
-    if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+    if (a.use_cond && bid == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
     return;
   }
   const double gam = st->gam, gam_old = st->gam_old, beta = st->beta;
@@ -212,8 +217,8 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a) {
   const long nsx = (nx + 31) / 32, nsm = (nm + kStencilStrip - 1) / kStencilStrip;
   const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz);
   double acc[2] = {0.0, 0.0};
-  for (long s = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
-       s += (long)gridDim.x * (blockDim.x >> 5)) {
+  for (long s = (long)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
+       s += (long)nblk * (blockDim.x >> 5)) {
     const int sx = (int)(s % nsx);
     const int sm = (int)((s / nsx) % nsm);
     const int yfix = DIM == 3 ? (int)(s / (nsx * nsm)) : 0;
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a) {
     }
   }
   double tot[2];
-  if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot)) return;
+  if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
   // scalar step after the stencil: delta_j and the stopping test for x_{iter}
   st->delta = tot[0] * inv_g * inv_g;
@@ -365,10 +370,14 @@ struct IngestArgs {
   int maxit;
 };
 
-static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a) {
+static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const IngestArgs* batch, int bps) {
+  const int sys = batch ? (int)(blockIdx.x / bps) : 0;
+  const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
+  const int nblk = batch ? bps : (int)gridDim.x;
+  const IngestArgs a = batch ? batch[sys] : a0;
   double acc[1] = {0.0};
   const double2 zero = make_double2(0.0, 0.0);
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < a.M; p += (long)gridDim.x * blockDim.x) {
+  for (long p = (long)bid * blockDim.x + threadIdx.x; p < a.M; p += (long)nblk * blockDim.x) {
     const double2 fv = a.f[p];
     const double2 bb = make_double2(fv.y, fv.x);
     a.b[p] = bb;
@@ -380,7 +389,7 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a) {
     acc[0] = fma(bb.x, bb.x, fma(bb.y, bb.y, acc[0]));
   }
   double tot[1];
-  if (!grid_sum_last_block<1>(acc, a.partials, &a.st->tickets[TICKET_INGEST], tot)) return;
+  if (!grid_sum_last_block<1>(acc, a.partials, &a.st->tickets[TICKET_INGEST], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
   DevState* st = a.st;
   st->bnorm = sqrt(tot[0]);

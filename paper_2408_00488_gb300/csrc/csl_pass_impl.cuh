@@ -7,17 +7,20 @@
 namespace csl {
 
 template <typename T, int N, bool W>
-cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s,
+                         const RowArgs<T>* batch, int nsys) {
+  const int grid = batch ? L.blocks * nsys : L.blocks;
+  const int bps = L.blocks;
   if (load == LOAD_V && store == STORE_T)
-    k_row<T, N, W, LOAD_V, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_V, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else if (load == LOAD_LANCZOS && store == STORE_T)
-    k_row<T, N, W, LOAD_LANCZOS, STORE_T><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_LANCZOS, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else if (load == LOAD_T && store == STORE_Z)
-    k_row<T, N, W, LOAD_T, STORE_Z><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_Z><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else if (load == LOAD_T && store == STORE_Z_UPDATE)
-    k_row<T, N, W, LOAD_T, STORE_Z_UPDATE><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_Z_UPDATE><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else if (load == LOAD_T && store == STORE_D)
-    k_row<T, N, W, LOAD_T, STORE_D><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_row<T, N, W, LOAD_T, STORE_D><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -25,14 +28,14 @@ cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLau
 
 template <typename T>
 cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
-                       cudaStream_t s) {
+                       cudaStream_t s, const RowArgs<T>* batch, int nsys) {
   switch (N) {
-#define CASE(NN)                                                  \
-  case NN:                                                        \
-    if constexpr (NN >= 512) {                                    \
-      if (wide) return launch_row_n<T, NN, true>(load, store, a, L, s); \
-    }                                                             \
-    return launch_row_n<T, NN, false>(load, store, a, L, s);
+#define CASE(NN)                                                                    \
+  case NN:                                                                          \
+    if constexpr (NN >= 512) {                                                      \
+      if (wide) return launch_row_n<T, NN, true>(load, store, a, L, s, batch, nsys); \
+    }                                                                               \
+    return launch_row_n<T, NN, false>(load, store, a, L, s, batch, nsys);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -40,24 +43,26 @@ cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& 
 }
 
 template <typename T, int N, bool W>
-cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s) {
+cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s,
+                             const StridedArgs<T>* batch, int nsys) {
+  const int grid = batch ? L.blocks * nsys : L.blocks;
   if (mid)
-    k_strided<T, N, W, true><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_strided<T, N, W, true><<<grid, L.threads, L.smem, s>>>(a, batch, L.blocks);
   else
-    k_strided<T, N, W, false><<<L.blocks, L.threads, L.smem, s>>>(a);
+    k_strided<T, N, W, false><<<grid, L.threads, L.smem, s>>>(a, batch, L.blocks);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
-                           cudaStream_t s) {
+                           cudaStream_t s, const StridedArgs<T>* batch, int nsys) {
   switch (N) {
-#define CASE(NN)                                                  \
-  case NN:                                                        \
-    if constexpr (NN >= 512) {                                    \
-      if (wide) return launch_strided_n<T, NN, true>(mid, a, L, s); \
-    }                                                             \
-    return launch_strided_n<T, NN, false>(mid, a, L, s);
+#define CASE(NN)                                                                  \
+  case NN:                                                                        \
+    if constexpr (NN >= 512) {                                                    \
+      if (wide) return launch_strided_n<T, NN, true>(mid, a, L, s, batch, nsys);  \
+    }                                                                             \
+    return launch_strided_n<T, NN, false>(mid, a, L, s, batch, nsys);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -100,9 +105,9 @@ cudaError_t set_pass_attrs() {
 }
 
 template cudaError_t launch_row<CSL_T>(int, bool, int, int, const RowArgs<CSL_T>&, const PassLaunch&,
-                                       cudaStream_t);
+                                       cudaStream_t, const RowArgs<CSL_T>*, int);
 template cudaError_t launch_strided<CSL_T>(int, bool, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
-                                           cudaStream_t);
+                                           cudaStream_t, const StridedArgs<CSL_T>*, int);
 template cudaError_t set_pass_attrs<CSL_T>();
 
 }  // namespace csl

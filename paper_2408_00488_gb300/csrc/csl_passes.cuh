@@ -77,9 +77,13 @@ __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
 template <typename T, int N, bool WIDE, int LOAD, int STORE>
-__global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
+__global__ void __launch_bounds__(256) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
+  const int sys = batch ? (int)(blockIdx.x / bps) : 0;
+  const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
+  const int nblk = batch ? bps : (int)gridDim.x;
+  const RowArgs<T> a = batch ? batch[sys] : a0;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
   constexpr int UB = NL < 8 ? NL : 8;      // load batch
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
   const int lpb = nlines;
   c_t* line = lines + (size_t)myl * LS;
   const int n = a.n;
-  for (int row0 = blockIdx.x * lpb; row0 < a.nrows; row0 += gridDim.x * lpb) {
+  for (int row0 = bid * lpb; row0 < a.nrows; row0 += nblk * lpb) {
     const int row = row0 + myl;
     const bool valid = row < a.nrows;
     const long base = (long)row * n;
@@ -204,9 +208,13 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a) {
 }
 
 template <typename T, int N, bool WIDE, bool MID>
-__global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
+__global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
+  const int sys = batch ? (int)(blockIdx.x / bps) : 0;
+  const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
+  const int nblk = batch ? bps : (int)gridDim.x;
+  const StridedArgs<T> a = batch ? batch[sys] : a0;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;
   constexpr int UB = NL < 8 ? NL : 8;
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
   const int ntx = (a.ncols + C - 1) / C;
   const int ntiles = ntx * a.nouter;
   double g2acc = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = bid; tile < ntiles; tile += nblk) {
     const int o = tile / ntx;
     const int col0 = (tile - o * ntx) * C;
     const int Ch = min(C, a.ncols - col0);
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a) {
   }
   if (!MID || a.scalar_mode == 0) return;
   double v[1] = {g2acc}, tot[1];
-  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot)) return;
+  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
   DevState* st = a.st;
   if (a.scalar_mode == 1) {  // gamma_1 = sqrt(<P^{-1} r0, r0>), start of MINRES
@@ -356,12 +364,14 @@ inline int pass_tpl(int N, bool wide) {
   return 1;
 }
 
+// batch (optional): device array of per-system arguments; the grid is then
+// L.blocks blocks per system times nsys
 template <typename T>
 cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
-                       cudaStream_t s);
+                       cudaStream_t s, const RowArgs<T>* batch = nullptr, int nsys = 0);
 template <typename T>
 cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
-                           cudaStream_t s);
+                           cudaStream_t s, const StridedArgs<T>* batch = nullptr, int nsys = 0);
 template <typename T>
 cudaError_t set_pass_attrs();
 
