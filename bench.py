@@ -17,6 +17,7 @@ Multi-GPU (torchrun, one rank per GPU): independent replicas of the solve
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -51,6 +52,33 @@ def read_peaks():
 # 152 SMs x 2 FP64 FMA/clk (x 2 flops) x 2.07 GHz, and 152 x 128 FP32 FMA/clk.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources: a committed ncu traffic figure is used only
+    while the kernels are unchanged since it was captured."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2408_00488_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_name, prec):
+    """DRAM bytes per launch of `kernel_name` (FP32/FP64 form of this
+    workload) from profiles/traffic.json, or None when absent or stale."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("kernels", {}).get(prec, {}).get(kernel_name)
 
 
 def golden_iters(name):
@@ -236,6 +264,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(name):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2408_00488_gb300 as csl
+
+    s = getattr(W, name)()
+    faces = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in s.faces]
+    f = torch.from_numpy(np.ascontiguousarray(s.f)).cuda()
+    for prec in ("fp32", "fp64"):
+        with csl.Plan(faces, s.lam, precision=prec) as plan:
+            plan.solve(f, tol=TOL, maxit=MAXIT)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("prof")
+            kt = plan.time_kernels(1)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            print(name, prec, plan.config, [(k, round(ms * 1e3, 1)) for k, ms in kt], flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -245,6 +294,12 @@ def main():
     ap.add_argument("--impl", default="csl", choices=["csl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven iteration loop (every kernel a separate launch, for launch lists)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched config-3 line")
+    ap.add_argument("--profile", choices=["config1", "config2"], default=None,
+                    help="solve once, then launch each kernel of one MINRES iteration (both forms) inside an "
+                         "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); no JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -258,6 +313,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
 
+    if args.profile:
+        run_profile(args.profile)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         if dist is not None:
@@ -310,7 +368,7 @@ def main():
     forms = {}
     plans = {}
     for prec in ("fp32", "fp64"):
-        plans[prec] = csl.Plan(faces, s.lam, precision=prec)
+        plans[prec] = csl.Plan(faces, s.lam, precision=prec, use_graph=not args.no_graph)
         z = torch.empty_like(f)
         for _ in range(args.warmup):
             _, info = plans[prec].solve(f, tol=TOL, maxit=MAXIT, out=z)
@@ -366,13 +424,40 @@ def main():
     head = kern["fp32_precond"]
     dom = max(head, key=lambda r: r["ms"])
     roofline = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"],
-                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
+                "traffic": committed_traffic(dom["kernel"], "fp32"),
                 "peak_source": (f"HBM {hbm_src} (MEASURED_PEAKS.json)" if dom["bound"] == "hbm" else
                                 "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.196 TFLOP/s)")}
     # whole-solve HBM fraction of the headline form: algorithmic bytes per iteration
     bytes_iter = sum(r["alg_bytes"] for r in head)
     solve_bytes = bytes_iter * info_mixed.iters
     hbm_pct_solve = solve_bytes / (ms_mixed / 1e3) / (hbm_gbs * 1e9)
+
+    # ---- batched shifts (config 3): 192 systems in one graph launch ---------
+    batched = None
+    if not args.no_batch:
+        systems = W.config3()
+        dfaces = {}
+        for sy in systems:
+            if id(sy.faces) not in dfaces:
+                dfaces[id(sy.faces)] = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in sy.faces]
+        fs = [torch.from_numpy(np.ascontiguousarray(sy.f)).to(dev) for sy in systems]
+        batched = {"workload": "config3: 2D n in {127,255,511} x 64 alpha-circulant shifts (L=64, eps=1e-4), "
+                               "a = 1+0.5 sin(pi x) sin(pi y), f ~ U[-1,1]^2 seed 3; 192 systems per step"}
+        for prec in ("fp32", "fp64"):
+            B = csl.Batch([(dfaces[id(sy.faces)], sy.lam) for sy in systems], precision=prec)
+            for _ in range(2):
+                B.solve(fs, tol=TOL, maxit=MAXIT)
+            barrier()
+            msb, infos = timed(lambda: B.solve(fs, tol=TOL, maxit=MAXIT)[1], max(2, args.steps // 2))
+            barrier()
+            msb = max_over_ranks(msb)
+            assert all(i.converged and i.relres <= TOL for i in infos)
+            its = [i.iters for i in infos]
+            batched[prec] = {"solves_per_s": world * len(systems) * 1e3 / msb, "ms_per_batch": msb,
+                             "iters_min": min(its), "iters_max": max(its),
+                             "max_relres": max(i.relres for i in infos)}
+            B.close()
 
     # ---- CPU baseline: the oracle on a bounded sample ----------------------
     cpu = None
@@ -397,6 +482,8 @@ def main():
             "forms": forms,
             "roofline": roofline,
             "solve_hbm_frac": round(hbm_pct_solve, 4),
+            "batched": batched,
+            "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
             "e2e": {"value": world * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,

@@ -31,7 +31,8 @@ class CSLSolve(torch.autograd.Function):
         y, info = plan.adjoint(grad_z.contiguous(), tol=ctx.tol, maxit=ctx.maxit)
         ctx.adjoint_info = info
         gfaces = plan.coef_grad(z, y)
-        plan.close()
+        # the plan lives as long as the autograd graph (backward may run more
+        # than once with retain_graph); Plan.__del__ releases it
         return (y, None, None, None, None) + tuple(gfaces)
 
 

@@ -191,15 +191,16 @@ def config4(n: int = 511):
     return System(2, n, faces, 1 + 20j, f), d
 
 
-def fd_directions(count: int, sizes: Sequence[int], seed: int = 6):
-    """`count` random unit directions over the concatenation of arrays of the
-    given sizes (standard normal, normalised)."""
+def fd_directions(count: int, sizes: Sequence[int], seed: int = 6, normalise: bool = False):
+    """`count` random directions over the concatenation of arrays of the given
+    sizes: i.i.d. standard normal entries, so that a step h moves every entry
+    by about h.  With normalise=True each direction has unit 2-norm instead."""
     rng = np.random.default_rng(seed)
     tot = int(sum(sizes))
     out = []
     for _ in range(count):
         d = rng.standard_normal(tot)
-        out.append(d / np.linalg.norm(d))
+        out.append(d / np.linalg.norm(d) if normalise else d)
     return out
 
 
