@@ -343,12 +343,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, K):
+    def timed(fn, K, tag):
         """K steps, each bracketed by CUDA events on the current stream, L2
-        flushed (outside the events) before every step; returns mean ms."""
+        flushed (outside the events) before every step; returns mean ms.  The
+        steps sit in the NVTX range `tag` (for ncu --nvtx-include "tag/")."""
         ms = []
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(tag)
         for _ in range(K):
             flush.zero_()
             e0.record()
@@ -356,6 +358,7 @@ def main():
             e1.record()
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
         return statistics.mean(ms), info
 
     def max_over_ranks(x):
@@ -385,7 +388,7 @@ def main():
     z = torch.empty_like(f)
     barrier()
     sampler.start()
-    ms_mixed, info_mixed = timed(lambda: plans["fp32"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps)
+    ms_mixed, info_mixed = timed(lambda: plans["fp32"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps, "timed_fp32")
     barrier()
     clocks = sampler.stop()
     ms_mixed = max_over_ranks(ms_mixed)
@@ -396,7 +399,7 @@ def main():
 
     # ---- plain FP64 form ---------------------------------------------------
     barrier()
-    ms_64, info_64 = timed(lambda: plans["fp64"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps)
+    ms_64, info_64 = timed(lambda: plans["fp64"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps, "timed_fp64")
     barrier()
     ms_64 = max_over_ranks(ms_64)
     assert info_64.converged and info_64.relres <= TOL
@@ -409,7 +412,7 @@ def main():
     for _ in range(2):
         plans["fp32"].solve_host(fh, zh, tol=TOL, maxit=MAXIT)
     barrier()
-    ms_e2e, info_e2e = timed(lambda: plans["fp32"].solve_host(fh, zh, tol=TOL, maxit=MAXIT), args.steps)
+    ms_e2e, info_e2e = timed(lambda: plans["fp32"].solve_host(fh, zh, tol=TOL, maxit=MAXIT), args.steps, "timed_e2e")
     barrier()
     ms_e2e = max_over_ranks(ms_e2e)
     assert info_e2e.converged
@@ -449,7 +452,7 @@ def main():
             for _ in range(2):
                 B.solve(fs, tol=TOL, maxit=MAXIT)
             barrier()
-            msb, infos = timed(lambda: B.solve(fs, tol=TOL, maxit=MAXIT)[1], max(2, args.steps // 2))
+            msb, infos = timed(lambda: B.solve(fs, tol=TOL, maxit=MAXIT)[1], max(2, args.steps // 2), "timed_batch_" + prec)
             barrier()
             msb = max_over_ranks(msb)
             assert all(i.converged and i.relres <= TOL for i in infos)
