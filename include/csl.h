@@ -62,8 +62,15 @@ typedef enum csl_status {
 
 typedef enum csl_precision {
   CSL_PREC_FP64 = 0,  /* every step in FP64 (the plain method)                          */
-  CSL_PREC_FP32 = 1   /* sine transforms and per-mode scale of P^{-1} in FP32; stencil,
+  CSL_PREC_FP32 = 1,  /* sine transforms and per-mode scale of P^{-1} in FP32; stencil,
                          Lanczos recurrence, Givens rotations and residual norms in FP64 */
+  CSL_PREC_BF16X3 = 2, /* as CSL_PREC_FP32, but the transforms along y and z (lines of
+                          n+1 = 32, 64 or 128 points) run on the tensor cores as GEMMs with
+                          the sine matrix of Section 2.3: operands split into two bf16 terms,
+                          3 products accumulated in FP32 (relative error about 1e-5).
+                          The paper has no such form (it ran FP64 throughout). */
+  CSL_PREC_BF16X6 = 3  /* as CSL_PREC_BF16X3 with three bf16 terms and 6 products
+                          (about FP32 accuracy) */
 } csl_precision;
 
 typedef struct csl_plan_options {

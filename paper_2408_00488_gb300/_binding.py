@@ -13,8 +13,8 @@ LIBPATH = os.path.join(HERE, "libcsl.so")
 
 OK, INVALID_ARG, UNSUPPORTED_SIZE, SINGULAR_PRECOND, BREAKDOWN, NOT_CONVERGED, TIMEOUT, CUDA_ERROR, \
     OUT_OF_MEMORY = range(9)
-PREC_FP64, PREC_FP32 = 0, 1
-_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32}
+PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
 
 
 class PlanOptions(ctypes.Structure):
@@ -149,8 +149,10 @@ class Plan:
     """A solver plan for one grid, coefficient field and shift lambda.
 
     faces: (x-faces, y-faces[, z-faces]) float64 CUDA tensors in the layout of
-    include/csl.h (x fastest).  precision: "fp64" or "fp32" (FP32 sine
-    transforms and scale inside P^{-1}; everything else FP64).
+    include/csl.h (x fastest).  precision: "fp64", "fp32" (FP32 sine
+    transforms and scale inside P^{-1}; everything else FP64), or "bf16x3" /
+    "bf16x6" (as "fp32", with the y and z transforms of lines of 32, 64 or
+    128 points as split-bf16 tensor-core GEMMs, 3 or 6 products).
     """
 
     def __init__(self, faces: Sequence, lam: complex, precision: str = "fp64",

@@ -117,6 +117,8 @@ struct csl_plan {
   void* tw[3] = {nullptr, nullptr, nullptr};
   void* hs[3] = {nullptr, nullptr, nullptr};
   void* tp[3] = {nullptr, nullptr, nullptr};
+  void* sine_tc[3] = {nullptr, nullptr, nullptr};  // tensor-core passes: split-bf16 sine matrix per axis
+  int tc_split = 0;                                // 2 or 3 bf16 terms (CSL_PREC_BF16X3 / X6), else 0
   double2 *b = nullptr, *x = nullptr, *io = nullptr;
   double2* v[2] = {nullptr, nullptr};
   double2* w[2] = {nullptr, nullptr};
@@ -164,6 +166,7 @@ cudaError_t set_attrs_once() {
   if (!done) {
     err = set_pass_attrs<double>();
     if (err == cudaSuccess) err = set_pass_attrs<float>();
+    if (err == cudaSuccess) err = set_tc_attrs();
     done = 1;
   }
   return err;
@@ -250,6 +253,7 @@ StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
   a.hs = (const T*)P->hs[axis];
   a.tp = (const typename C2<T>::t*)P->tp[axis] + (c.wide ? line_tp_size(c.N, false) : 0);
   a.data = (typename C2<T>::t*)P->T;
+  a.sine_tc = P->sine_tc[axis];
   return a;
 }
 
@@ -359,7 +363,7 @@ cudaError_t launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_co
 }
 
 cudaError_t launch_iteration(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
-  if (P->precision == CSL_PREC_FP32) return launch_iteration_T<float>(P, par, s, use_cond);
+  if (P->precision != CSL_PREC_FP64) return launch_iteration_T<float>(P, par, s, use_cond);
   return launch_iteration_T<double>(P, par, s, use_cond);
 }
 
@@ -400,7 +404,7 @@ cudaError_t launch_prologue_T(csl_plan* P, const double2* f, double tol, int max
 }
 
 cudaError_t launch_prologue(csl_plan* P, const double2* f, double tol, int maxit, double beta, cudaStream_t s) {
-  if (P->precision == CSL_PREC_FP32) return launch_prologue_T<float>(P, f, tol, maxit, beta, s);
+  if (P->precision != CSL_PREC_FP64) return launch_prologue_T<float>(P, f, tol, maxit, beta, s);
   return launch_prologue_T<double>(P, f, tol, maxit, beta, s);
 }
 
@@ -460,6 +464,7 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
 template <typename T>
 cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e0, cudaEvent_t e1,
                       const DevState& hst) {
+  if (c.L.tc) return cudaSuccess;  // the tensor-core variant has one launch shape
   const TuneKey key = {(int)sizeof(T), kind, c.N, c.ncols, c.nouter};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -690,7 +695,9 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   csl_plan_options o;
   csl_plan_options_init(&o);
   if (opt) o = *opt;
-  if (o.precision != CSL_PREC_FP64 && o.precision != CSL_PREC_FP32) return CSL_INVALID_ARG;
+  if (o.precision != CSL_PREC_FP64 && o.precision != CSL_PREC_FP32 && o.precision != CSL_PREC_BF16X3 &&
+      o.precision != CSL_PREC_BF16X6)
+    return CSL_INVALID_ARG;
   CSL_TRY(set_attrs_once());
 
   csl_plan* P = new (std::nothrow) csl_plan();
@@ -709,7 +716,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   const long M = P->M;
   const int nx = P->n[0], ny = P->n[1], nz = P->n[2];
-  const size_t tsz = o.precision == CSL_PREC_FP32 ? sizeof(float) : sizeof(double);
+  const size_t tsz = o.precision != CSL_PREC_FP64 ? sizeof(float) : sizeof(double);
   long nface[3];
   nface[0] = (long)nz * ny * (nx + 1);
   nface[1] = (long)nz * (ny + 1) * nx;
@@ -825,7 +832,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     make_tp_table(N, tpd);
     const size_t ntp = tpd.size();
     if (ntp) {
-      if (o.precision == CSL_PREC_FP32) {
+      if (o.precision != CSL_PREC_FP64) {
         std::vector<float> tpf(ntp);
         for (size_t i = 0; i < ntp; ++i) tpf[i] = (float)tpd[i];
         err = cudaMemcpy(P->tp[d], tpf.data(), ntp * 4, cudaMemcpyHostToDevice);
@@ -836,7 +843,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     }
     err = cudaMemcpy(P->mu_d[d], mu.data(), nd * 8, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(P->mu_f[d], muf.data(), nd * 4, cudaMemcpyHostToDevice);
-    if (o.precision == CSL_PREC_FP32) {
+    if (o.precision != CSL_PREC_FP64) {
       std::vector<float> twf(N), hsf(N / 2 + 1);
       for (int i = 0; i < N; ++i) twf[i] = (float)twd[i];
       for (int j = 0; j <= N / 2; ++j) hsf[j] = (float)hsd[j];
@@ -884,7 +891,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   // launch configurations of the sine-transform passes
   const long nrows = M / nx;
-  if (o.precision == CSL_PREC_FP32) {
+  if (o.precision != CSL_PREC_FP64) {
     config_row<float>(P->row, nx, (int)nrows);
     if (dim == 2) {
       config_strided<float>(P->sy, ny, nx, 1, 0, nx, o.lines_per_cta);
@@ -901,9 +908,45 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       config_strided<double>(P->sz, nz, nx, ny, nx, (long)nx * ny, o.lines_per_cta);
     }
   }
+  // split-BF16 tensor-core variant of the strided passes (lines of N <= 128)
+  if (o.precision == CSL_PREC_BF16X3 || o.precision == CSL_PREC_BF16X6) {
+    P->tc_split = o.precision == CSL_PREC_BF16X3 ? 2 : 3;
+    PassCfg* sc[3] = {nullptr, &P->sy, &P->sz};
+    for (int d = 1; d < dim && err == cudaSuccess; ++d) {
+      PassCfg& c = *sc[d];
+      if (!tc_supported(c.N)) continue;
+      const bool mid = (d == dim - 1);
+      void* img_dev = nullptr;
+      for (int e2 = 1; e2 < d; ++e2)
+        if (P->sine_tc[e2] && sc[e2]->N == c.N) img_dev = P->sine_tc[e2];
+      if (!img_dev) {
+        std::vector<uint16_t> img;
+        build_sine_image(c.N, P->tc_split, img);
+        img_dev = dalloc(P, img.size() * sizeof(uint16_t), &err);
+        if (err == cudaSuccess)
+          err = cudaMemcpy(img_dev, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+      }
+      P->sine_tc[d] = img_dev;
+      const long tiles = (long)((c.ncols + 63) / 64) * c.nouter;
+      long cap = (long)kSMs * tc_ctas_per_sm(c.N, P->tc_split, mid);
+      if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+      c.L.blocks = (int)(tiles < cap ? tiles : cap);
+      c.L.threads = 256;
+      c.L.smem = tc_smem_bytes(c.N, P->tc_split);
+      c.L.tc = P->tc_split;
+      c.lines = 64;
+      c.wide = false;
+    }
+    if (err != cudaSuccess) {
+      CSL_NOTE(err, "tensor-core sine tables");
+      (void)cudaGetLastError();
+      free_plan(P);
+      return CSL_CUDA_ERROR;
+    }
+  }
   if (o.autotune && o.lines_per_cta <= 0) {
     // (the chosen shapes are described in P->config below)
-    err = o.precision == CSL_PREC_FP32 ? autotune<float>(P) : autotune<double>(P);
+    err = o.precision != CSL_PREC_FP64 ? autotune<float>(P) : autotune<double>(P);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) {
       CSL_NOTE(err, "autotune");
@@ -915,13 +958,20 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   {
     const PassCfg* cs[3] = {&P->row, &P->sy, &P->sz};
     const char* nm[3] = {"x", "y", "z"};
-    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[blocks=%d]",
-                       o.precision == CSL_PREC_FP32 ? "fp32" : "fp64", o.autotune ? " autotuned" : "",
-                       P->sten_blocks);
+    const char* pname = o.precision == CSL_PREC_FP64     ? "fp64"
+                        : o.precision == CSL_PREC_FP32   ? "fp32"
+                        : o.precision == CSL_PREC_BF16X3 ? "bf16x3"
+                                                         : "bf16x6";
+    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[blocks=%d]", pname,
+                       o.autotune ? " autotuned" : "", P->sten_blocks);
     for (int d = 0; d < dim && off < (int)sizeof(P->config); ++d)
       off += snprintf(P->config + off, sizeof(P->config) - off, " %s[N=%d %s lines=%d threads=%d blocks=%d smem=%zu]",
-                      nm[d], cs[d]->N, cs[d]->wide ? "stockham64" : "warp", cs[d]->lines, cs[d]->L.threads,
-                      cs[d]->L.blocks, cs[d]->L.smem);
+                      nm[d], cs[d]->N,
+                      cs[d]->L.tc == 2   ? "tcgen05-bf16x3"
+                      : cs[d]->L.tc == 3 ? "tcgen05-bf16x6"
+                      : cs[d]->wide      ? "stockham64"
+                                         : "warp",
+                      cs[d]->lines, cs[d]->L.threads, cs[d]->L.blocks, cs[d]->L.smem);
   }
   *out = P;
   return CSL_OK;
@@ -964,7 +1014,7 @@ csl_status csl_apply(csl_plan* P, const double* z, double* out) {
 
 csl_status csl_precondition(csl_plan* P, const double* v, double* out) {
   if (!P || !v || !out) return CSL_INVALID_ARG;
-  if (P->precision == CSL_PREC_FP32)
+  if (P->precision != CSL_PREC_FP64)
     CSL_TRY(launch_precondition_T<float>(P, (const double2*)v, (double2*)out, P->stream));
   else
     CSL_TRY(launch_precondition_T<double>(P, (const double2*)v, (double2*)out, P->stream));
@@ -1040,7 +1090,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  const bool fp32 = P->precision == CSL_PREC_FP32;
+  const bool fp32 = P->precision != CSL_PREC_FP64;
   const int nk = P->dim == 2 ? 4 : 6;
   static const char* n2[4] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
                               "k_row<LOAD_T,STORE_Z_UPDATE>"};
@@ -1548,7 +1598,7 @@ csl_status csl_batch_create(csl_batch** out, int nsys, const csl_system_desc* sy
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.branch, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming);
     if (e == cudaSuccess)
-      e = o.precision == CSL_PREC_FP32 ? build_group_args<float>(B, G) : build_group_args<double>(B, G);
+      e = o.precision != CSL_PREC_FP64 ? build_group_args<float>(B, G) : build_group_args<double>(B, G);
   }
   if (e != cudaSuccess) {
     CSL_NOTE(e, "csl_batch_create");
@@ -1565,7 +1615,7 @@ csl_status csl_batch_solve(csl_batch* B, const double* const* f, double* const* 
   if (!B || !f || !z || !(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
   for (int i = 0; i < B->nsys; ++i)
     if (!f[i] || !z[i]) return CSL_INVALID_ARG;
-  return B->precision == CSL_PREC_FP32 ? batch_solve_T<float>(B, f, z, tol, maxit, infos)
+  return B->precision != CSL_PREC_FP64 ? batch_solve_T<float>(B, f, z, tol, maxit, infos)
                                        : batch_solve_T<double>(B, f, z, tol, maxit, infos);
 }
 

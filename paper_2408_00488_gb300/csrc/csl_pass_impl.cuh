@@ -56,6 +56,9 @@ cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch
 template <typename T>
 cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
                            cudaStream_t s, const StridedArgs<T>* batch, int nsys) {
+  if constexpr (sizeof(T) == 4) {
+    if (L.tc) return launch_strided_tc(N, L.tc, mid, a, L, s, batch, nsys);
+  }
   switch (N) {
 #define CASE(NN)                                                                  \
   case NN:                                                                        \

@@ -16,6 +16,8 @@
 #include "csl_fft.cuh"
 #include "csl_kernels.cuh"
 
+#include <vector>
+
 namespace csl {
 
 enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2 };
@@ -58,6 +60,7 @@ struct StridedArgs {
   DevState* st;
   double* partials;
   int scalar_mode;     // 0 none, 1 init (gamma_1), 2 MINRES iteration
+  const void* sine_tc; // tensor-core variant: split-bf16 sine matrix in B-operand layout
 };
 
 // byte offsets of the shared-memory regions: twiddles | half sines | extra
@@ -207,6 +210,34 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a0, const RowArgs<T>* ba
   }
 }
 
+// End of a MID pass: grid sum of the Parseval partials; the last CTA either
+// starts MINRES (scalar_mode 1: gamma_1 = sqrt(<P^{-1} r0, r0>)) or runs the
+// Givens step of the iteration (scalar_mode 2).
+template <typename T>
+__device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, int nblk) {
+  double v[1] = {g2acc}, tot[1];
+  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot, bid, nblk)) return;
+  if (threadIdx.x != 0) return;
+  DevState* st = a.st;
+  if (a.scalar_mode == 1) {
+    const double g2 = tot[0];
+    if (!(g2 > 0.0) || !(g2 < 1e300)) {
+      st->done = 1;
+      st->status = (g2 == 0.0) ? ST_OK : ST_BREAKDOWN;
+      st->relres = (g2 == 0.0) ? 0.0 : st->relres;
+      return;
+    }
+    st->gam = sqrt(g2);
+    st->gam1 = st->gam;
+    st->gam_old = 1.0;
+    st->eta = st->gam;
+    st->eta_x = st->gam;
+    st->rho = st->bnorm / st->gam;  // exact at x_0 = 0
+    return;
+  }
+  givens_step(st, tot[0]);
+}
+
 template <typename T, int N, bool WIDE, bool MID>
 __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
@@ -293,28 +324,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a0, const Stride
       if (c < Ch) a.data[base + (long)j * a.line_stride + c] = lines[(size_t)c * LS + D::out_pos(j + 1)];
     }
   }
-  if (!MID || a.scalar_mode == 0) return;
-  double v[1] = {g2acc}, tot[1];
-  if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot, bid, nblk)) return;
-  if (threadIdx.x != 0) return;
-  DevState* st = a.st;
-  if (a.scalar_mode == 1) {  // gamma_1 = sqrt(<P^{-1} r0, r0>), start of MINRES
-    const double g2 = tot[0];
-    if (!(g2 > 0.0) || !(g2 < 1e300)) {
-      st->done = 1;
-      st->status = (g2 == 0.0) ? ST_OK : ST_BREAKDOWN;
-      st->relres = (g2 == 0.0) ? 0.0 : st->relres;
-      return;
-    }
-    st->gam = sqrt(g2);
-    st->gam1 = st->gam;
-    st->gam_old = 1.0;
-    st->eta = st->gam;
-    st->eta_x = st->gam;
-    st->rho = st->bnorm / st->gam;  // exact at x_0 = 0
-    return;
-  }
-  givens_step(st, tot[0]);
+  if (MID && a.scalar_mode != 0) mid_scalar_tail<T>(a, g2acc, bid, nblk);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,6 +333,7 @@ __global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a0, const Stride
 struct PassLaunch {
   int blocks, threads;
   size_t smem;
+  int tc = 0;  // strided passes: 0 = FFT, 2 or 3 = tensor-core GEMM with that many bf16 terms
 };
 
 #define CSL_FOR_EACH_N(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
@@ -374,5 +385,14 @@ cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, 
                            cudaStream_t s, const StridedArgs<T>* batch = nullptr, int nsys = 0);
 template <typename T>
 cudaError_t set_pass_attrs();
+
+// tensor-core strided passes (csl_tc.cu): lines of N = 32, 64 or 128 points
+bool tc_supported(int N);
+size_t tc_smem_bytes(int N, int split);
+int tc_ctas_per_sm(int N, int split, bool mid);
+cudaError_t launch_strided_tc(int N, int split, bool mid, const StridedArgs<float>& a, const PassLaunch& L,
+                              cudaStream_t s, const StridedArgs<float>* batch, int nsys);
+cudaError_t set_tc_attrs();
+void build_sine_image(int N, int split, std::vector<uint16_t>& img);
 
 }  // namespace csl
