@@ -274,7 +274,7 @@ def run_profile(name):
     s = getattr(W, name)()
     faces = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in s.faces]
     f = torch.from_numpy(np.ascontiguousarray(s.f)).cuda()
-    for prec in ("fp32", "fp64"):
+    for prec in (("fp32", "fp64") if name == "config1" else ("bf16x6", "bf16x3", "fp32")):
         with csl.Plan(faces, s.lam, precision=prec) as plan:
             plan.solve(f, tol=TOL, maxit=MAXIT)
             torch.cuda.synchronize()
@@ -297,9 +297,11 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven iteration loop (every kernel a separate launch, for launch lists)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched config-3 line")
+    ap.add_argument("--no-config2", action="store_true", help="skip the config-2 forms (FFT vs tensor-core DST)")
     ap.add_argument("--profile", choices=["config1", "config2"], default=None,
-                    help="solve once, then launch each kernel of one MINRES iteration (both forms) inside an "
-                         "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); no JSON")
+                    help="solve once, then launch each kernel of one MINRES iteration inside an "
+                         "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32 "
+                         "and fp64 forms, config2: bf16x6, bf16x3 and fp32; no JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -447,7 +449,7 @@ def main():
         fs = [torch.from_numpy(np.ascontiguousarray(sy.f)).to(dev) for sy in systems]
         batched = {"workload": "config3: 2D n in {127,255,511} x 64 alpha-circulant shifts (L=64, eps=1e-4), "
                                "a = 1+0.5 sin(pi x) sin(pi y), f ~ U[-1,1]^2 seed 3; 192 systems per step"}
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp32", "bf16x6", "fp64"):
             B = csl.Batch([(dfaces[id(sy.faces)], sy.lam) for sy in systems], precision=prec)
             for _ in range(2):
                 B.solve(fs, tol=TOL, maxit=MAXIT)
@@ -461,6 +463,31 @@ def main():
                              "iters_min": min(its), "iters_max": max(its),
                              "max_relres": max(i.relres for i in infos)}
             B.close()
+
+    # ---- config 2 (3D n = 127): FFT vs split-BF16 tensor-core transforms ---
+    cfg2 = None
+    if not args.no_config2:
+        s2 = W.config2()
+        faces2 = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in s2.faces]
+        f2 = torch.from_numpy(np.ascontiguousarray(s2.f)).to(dev)
+        z2 = torch.empty_like(f2)
+        cfg2 = {"workload": "config2: 3D n=127 (M=2,048,383), a = 1+0.9 sin2pix sin2piy sin2piz at face midpoints, "
+                            "lambda=-5+50i, f ~ N(0,1)^2 seed 2, tol 1e-8"}
+        for prec in ("fp64", "fp32", "bf16x3", "bf16x6"):
+            p2 = csl.Plan(faces2, s2.lam, precision=prec)
+            for _ in range(2):
+                p2.solve(f2, tol=TOL, maxit=MAXIT, out=z2)
+            barrier()
+            ms2, inf2 = timed(lambda: p2.solve(f2, tol=TOL, maxit=MAXIT, out=z2)[1], max(3, args.steps // 2),
+                              "timed_c2_" + prec)
+            barrier()
+            ms2 = max_over_ranks(ms2)
+            assert inf2.converged and inf2.relres <= TOL
+            kt = p2.time_kernels(args.kernel_reps)
+            cfg2[prec] = {"solves_per_s": world * 1e3 / ms2, "ms_per_solve": ms2, "iters": inf2.iters,
+                          "relres": inf2.relres, "us_per_iter": ms2 * 1e3 / inf2.iters,
+                          "kernels_us": {k: round(ms * 1e3, 1) for k, ms in kt}, "plan": p2.config}
+            p2.close()
 
     # ---- CPU baseline: the oracle on a bounded sample ----------------------
     cpu = None
@@ -486,6 +513,7 @@ def main():
             "roofline": roofline,
             "solve_hbm_frac": round(hbm_pct_solve, 4),
             "batched": batched,
+            "config2_forms": cfg2,
             "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
