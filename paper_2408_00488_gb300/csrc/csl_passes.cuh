@@ -18,6 +18,10 @@
 
 #include <vector>
 
+// FP32 passes: two CTAs of 256 threads per SM (at most 128 registers per
+// thread); the FP64 lines need the full register file
+#define CSL_PASS_MINB(T) (sizeof(T) == 4 ? 2 : 1)
+
 namespace csl {
 
 enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2 };
@@ -80,7 +84,7 @@ __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
 template <typename T, int N, bool WIDE, int LOAD, int STORE>
-__global__ void __launch_bounds__(256) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
+__global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -89,7 +93,10 @@ __global__ void __launch_bounds__(256) k_row(RowArgs<T> a0, const RowArgs<T>* ba
   const RowArgs<T> a = batch ? batch[sys] : a0;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
-  constexpr int UB = NL < 8 ? NL : 8;      // load batch
+  // load batch: the Lanczos and update variants keep 2 and 4 FP64 vectors per
+  // element in flight, so they batch fewer elements (128-register FP32 budget)
+  constexpr int UBMAX = STORE == STORE_Z_UPDATE ? 2 : LOAD == LOAD_LANCZOS ? 4 : 8;
+  constexpr int UB = NL < UBMAX ? NL : UBMAX;
   if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* s_tw = (c_t*)smem_raw;
@@ -239,7 +246,7 @@ __device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, 
 }
 
 template <typename T, int N, bool WIDE, bool MID>
-__global__ void __launch_bounds__(256) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
+__global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
