@@ -285,6 +285,38 @@ def run_profile(name):
             print(name, prec, plan.config, [(k, round(ms * 1e3, 1)) for k, ms in kt], flush=True)
 
 
+# ---- replicas (one process per GPU; no data-path collective) ---------------
+def init_replicas(backend):
+    """Rank, world size, local rank and the torch.distributed module (None for
+    a single process) from the torchrun environment; one GPU per rank."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    return rank, world, local_rank, dist
+
+
+def replica_max(x, dist, device="cpu"):
+    """The slowest replica's time: maximum of a per-rank float over all ranks."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * 1e3 / ms_max
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -305,15 +337,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        import torch
-        torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl")
+    rank, world, local_rank, dist = init_replicas("nccl")
 
     if args.profile:
         run_profile(args.profile)
@@ -364,11 +388,7 @@ def main():
         return statistics.mean(ms), info
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(x, dist, dev)
 
     forms = {}
     plans = {}
@@ -395,7 +415,7 @@ def main():
     clocks = sampler.stop()
     ms_mixed = max_over_ranks(ms_mixed)
     assert info_mixed.converged and info_mixed.relres <= TOL
-    forms["fp32_precond"] = {"solves_per_s": world * 1e3 / ms_mixed, "ms_per_solve": ms_mixed,
+    forms["fp32_precond"] = {"solves_per_s": job_rate(1, world, ms_mixed), "ms_per_solve": ms_mixed,
                              "iters": info_mixed.iters, "relres": info_mixed.relres,
                              "launches_per_solve": info_mixed.launches}
 
@@ -405,7 +425,7 @@ def main():
     barrier()
     ms_64 = max_over_ranks(ms_64)
     assert info_64.converged and info_64.relres <= TOL
-    forms["fp64"] = {"solves_per_s": world * 1e3 / ms_64, "ms_per_solve": ms_64, "iters": info_64.iters,
+    forms["fp64"] = {"solves_per_s": job_rate(1, world, ms_64), "ms_per_solve": ms_64, "iters": info_64.iters,
                      "relres": info_64.relres, "launches_per_solve": info_64.launches}
 
     # ---- end to end through the C ABI with host buffers (pinned) -------------
@@ -459,7 +479,7 @@ def main():
             msb = max_over_ranks(msb)
             assert all(i.converged and i.relres <= TOL for i in infos)
             its = [i.iters for i in infos]
-            batched[prec] = {"solves_per_s": world * len(systems) * 1e3 / msb, "ms_per_batch": msb,
+            batched[prec] = {"solves_per_s": job_rate(len(systems), world, msb), "ms_per_batch": msb,
                              "iters_min": min(its), "iters_max": max(its),
                              "max_relres": max(i.relres for i in infos)}
             B.close()
@@ -484,7 +504,7 @@ def main():
             ms2 = max_over_ranks(ms2)
             assert inf2.converged and inf2.relres <= TOL
             kt = p2.time_kernels(args.kernel_reps)
-            cfg2[prec] = {"solves_per_s": world * 1e3 / ms2, "ms_per_solve": ms2, "iters": inf2.iters,
+            cfg2[prec] = {"solves_per_s": job_rate(1, world, ms2), "ms_per_solve": ms2, "iters": inf2.iters,
                           "relres": inf2.relres, "us_per_iter": ms2 * 1e3 / inf2.iters,
                           "kernels_us": {k: round(ms * 1e3, 1) for k, ms in kt}, "plan": p2.config}
             p2.close()
@@ -503,7 +523,7 @@ def main():
     if rank == 0:
         bytes_io = 16 * M
         line = {
-            "metric": METRIC, "value": world * 1e3 / ms_mixed, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_rate(1, world, ms_mixed), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 inside P^-1)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32-preconditioner MINRES (FP64 stencil/Lanczos/Givens)",
@@ -517,7 +537,7 @@ def main():
             "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+            "e2e": {"value": job_rate(1, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
             "gpu_launches": info_mixed.launches * args.steps,
             "clocks": clocks,

@@ -372,3 +372,52 @@ def test_workload_shifts_and_determinism():
     a = W.rhs_uniform((4, 4), 3)
     b = W.rhs_uniform((4, 4), 3)
     assert np.array_equal(a, b) and np.abs(a.real).max() <= 1
+
+
+# --- rectangular grids (n_x != n_y [!= n_z], h_a = 1/(n_a + 1) per axis) ---
+def _tridiag_laplacian(n, h):
+    return (2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)) / (h * h)
+
+
+@pytest.mark.parametrize("ns", [(5, 3), (3, 7), (4, 3, 2), (2, 5, 3)])
+def test_rectangular_K_is_kronecker_sum(ns):
+    """a = 1 on an n_x x n_y (x n_z) grid: K is the Kronecker sum of the 1D
+    Dirichlet Laplacians, each with its own spacing (x fastest in C order)."""
+    dim = len(ns)
+    faces = W.sample_faces(dim, ns, W.coef_const(1.0))
+    K = O.assemble_K_dense(faces)
+    T = [_tridiag_laplacian(n, 1.0 / (n + 1)) for n in ns]
+    I = [np.eye(n) for n in ns]
+    if dim == 2:
+        ref = np.kron(I[1], T[0]) + np.kron(T[1], I[0])
+    else:
+        ref = (np.kron(np.kron(I[2], I[1]), T[0]) + np.kron(np.kron(I[2], T[1]), I[0]) +
+               np.kron(np.kron(T[2], I[1]), I[0]))
+    assert np.allclose(K, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("ns", [(7, 3), (3, 15), (7, 3, 5)])
+def test_rectangular_laplacian_eigs_closed_form(ns):
+    """The sine transform's eigenvalues sum_a 4/h_a^2 sin^2(k_a pi / (2(n_a+1)))
+    are the spectrum of the dense rectangular Laplacian."""
+    dim = len(ns)
+    faces = W.sample_faces(dim, ns, W.coef_const(1.0))
+    K = O.assemble_K_dense(faces)
+    shape = W.grid_array_shape(dim, ns)
+    mu = np.sort(O.laplacian_eigs(shape).ravel())
+    ev = np.sort(np.linalg.eigvalsh(K))
+    assert np.allclose(mu, ev, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("ns,coef,lam", [((7, 3), W.coef_c1, 100j), ((3, 7), W.coef_c0, -5 + 50j),
+                                         ((3, 7, 5), W.coef_c2, 1 + 10j)])
+def test_rectangular_solve_matches_dense_lu(ns, coef, lam):
+    dim = len(ns)
+    faces = W.sample_faces(dim, ns, coef)
+    shape = W.grid_array_shape(dim, ns)
+    f = W.rhs_uniform(shape, 35)
+    z, info = O.solve(faces, lam, f, 1e-12, 500)
+    K = O.assemble_K_dense(faces)
+    zr = np.linalg.solve(K + lam * np.eye(K.shape[0]), f.ravel()).reshape(shape)
+    assert info.converged
+    assert np.linalg.norm(z - zr) / np.linalg.norm(zr) < 1e-9

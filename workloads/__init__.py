@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Callable, Optional, Sequence
+from typing import Callable, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -33,31 +33,50 @@ def grid_h(n: int) -> float:
     return 1.0 / (n + 1)
 
 
-def face_coordinates(dim: int, n: int, axis: int):
+def axis_sizes(dim: int, n) -> Tuple[int, ...]:
+    """Points per spatial axis (x, y[, z]): n is one int (square / cube grid)
+    or a sequence (nx, ny[, nz]) for a rectangular grid."""
+    if isinstance(n, (int, np.integer)):
+        return (int(n),) * dim
+    t = tuple(int(v) for v in n)
+    assert len(t) == dim
+    return t
+
+
+def face_coordinates(dim: int, n, axis: int):
     """Coordinates of the face midpoints normal to spatial axis `axis`
     (0 = x, 1 = y, 2 = z) as a list of broadcastable arrays ordered (x, y, z),
-    each shaped like the face array (C-order, x fastest)."""
-    h = grid_h(n)
+    each shaped like the face array (C-order, x fastest).  Axis a has
+    n_a points and spacing h_a = 1/(n_a + 1)."""
+    ns = axis_sizes(dim, n)
     coords = []
     for a in range(dim):
+        h = grid_h(ns[a])
         if a == axis:
-            c = (np.arange(n + 1, dtype=np.float64) + 0.5) * h
+            c = (np.arange(ns[a] + 1, dtype=np.float64) + 0.5) * h
         else:
-            c = (np.arange(n, dtype=np.float64) + 1.0) * h
+            c = (np.arange(ns[a], dtype=np.float64) + 1.0) * h
         shape = [1] * dim
         shape[dim - 1 - a] = c.size  # spatial axis a is numpy axis dim-1-a
         coords.append(c.reshape(shape))
     return coords
 
 
-def sample_faces(dim: int, n: int, coef: Callable[..., np.ndarray]):
+def grid_array_shape(dim: int, n) -> Tuple[int, ...]:
+    """numpy shape of a grid vector: (ny, nx) or (nz, ny, nx)."""
+    return tuple(reversed(axis_sizes(dim, n)))
+
+
+def sample_faces(dim: int, n, coef: Callable[..., np.ndarray]):
     """Sample a(x[, y[, z]]) at every face midpoint; returns a tuple of
-    float64 C-contiguous arrays ordered (x-faces, y-faces[, z-faces])."""
+    float64 C-contiguous arrays ordered (x-faces, y-faces[, z-faces]).  n is
+    one int or the per-axis sizes (nx, ny[, nz])."""
+    ns = axis_sizes(dim, n)
     out = []
     for axis in range(dim):
-        c = face_coordinates(dim, n, axis)
-        shape = [n] * dim
-        shape[dim - 1 - axis] = n + 1
+        c = face_coordinates(dim, ns, axis)
+        shape = list(reversed(ns))
+        shape[dim - 1 - axis] += 1
         vals = np.broadcast_to(np.asarray(coef(*c), dtype=np.float64), shape)
         out.append(np.ascontiguousarray(vals))
     return tuple(out)
