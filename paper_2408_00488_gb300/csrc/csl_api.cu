@@ -48,7 +48,7 @@ const double kNaN = __builtin_nan("");
 // one sine-transform pass: line length N = n + 1, CTA shape and grid
 struct PassCfg {
   int N = 0, n = 0, lines = 0;  // lines per CTA
-  bool wide = false;             // two-warp Stockham transform (N = 512, 1024) instead of warp per line
+  int wide = 0;                  // N = 512, 1024: 0 warp per line, 1 / 2 Stockham with 64 / 128 lanes per line
   int ncols = 0, nouter = 0;     // strided: x extent and outer blocks; row: nouter = rows
   long outer_stride = 0, line_stride = 0;
   PassLaunch L = {1, 32, 0};
@@ -476,12 +476,12 @@ cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e
   }
   PassCfg best = c;
   float best_ms = 1e30f;
-  for (int w = 0; w < (pass_has_wide(c.N) ? 2 : 1); ++w) {
-    const int tpl = pass_tpl(c.N, w == 1);
+  for (int w = 0; w < pass_num_variants(c.N); ++w) {
+    const int tpl = pass_tpl(c.N, w);
     for (int lines = 1; lines * tpl <= 256; lines <<= 1) {
       if (lines * tpl < 32) continue;
       PassCfg cand = c;
-      cand.wide = (w == 1);
+      cand.wide = w;
       cand.lines = lines;
       cand.L.threads = lines * tpl;
       cand.L.smem = pass_smem<T>(c.N, cand.wide, lines);
@@ -935,7 +935,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       c.L.smem = tc_smem_bytes(c.N, P->tc_split);
       c.L.tc = P->tc_split;
       c.lines = 64;
-      c.wide = false;
+      c.wide = 0;
     }
     if (err != cudaSuccess) {
       CSL_NOTE(err, "tensor-core sine tables");
@@ -969,7 +969,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
                       nm[d], cs[d]->N,
                       cs[d]->L.tc == 2   ? "tcgen05-bf16x3"
                       : cs[d]->L.tc == 3 ? "tcgen05-bf16x6"
-                      : cs[d]->wide      ? "stockham64"
+                      : cs[d]->wide == 2 ? "stockham128"
+                      : cs[d]->wide == 1 ? "stockham64"
                                          : "warp",
                       cs[d]->lines, cs[d]->L.threads, cs[d]->L.blocks, cs[d]->L.smem);
   }

@@ -259,25 +259,29 @@ __device__ __forceinline__ void dst_line(typename C2<T>::t* a, int t, const type
 }
 
 // ---------------------------------------------------------------------------
-// Wide path (N = 512, 1024): 64 lanes (two warps) per line, a three-pass
-// Stockham autosort FFT with radices R0 x R1 x R2, CTA-wide barriers.  On a
-// 2D grid there are only n lines per pass, so one warp per line leaves most
-// of the GPU idle; two warps per line halve the per-line latency and double
-// the warps in flight.  Pass p (Ls = R0..R_{p-1}, radix r) takes butterfly l
-// = j Ls + k, reads x[l + q N/r] (q < r), multiplies by w_{Ls r}^{q k} (table
-// [q][k], conflict-free), transforms over q and writes x[j Ls r + k + s Ls].
-// Shared-memory indices are padded by one slot per 32 (wpad) so the strided
-// stores of the early passes spread over the banks.
+// Wide paths (N = 512, 1024): TPL = 64 or 128 lanes (two or four warps) per
+// line, a three-pass Stockham autosort FFT with radices R0 x R1 x R2,
+// CTA-wide barriers.  On a 2D grid there are only n lines per pass, so one
+// warp per line leaves most of the GPU idle; more lanes per line cut the
+// per-line latency and multiply the warps in flight.  Pass p (Ls =
+// R0..R_{p-1}, radix r) takes butterfly l = j Ls + k (l < N/r; lanes beyond
+// that idle in the pass), reads x[l + q N/r] (q < r), multiplies by
+// w_{Ls r}^{q k} (table [q][k], conflict-free), transforms over q and writes
+// x[j Ls r + k + s Ls].  Shared-memory indices are padded by one slot per 32
+// (wpad) so the strided stores of the early passes spread over the banks.
 // ---------------------------------------------------------------------------
 template <int N> struct WideShape;
-template <> struct WideShape<512> { enum { TPL = 64, R0 = 8, R1 = 8, R2 = 8 }; };
-template <> struct WideShape<1024> { enum { TPL = 64, R0 = 8, R1 = 8, R2 = 16 }; };
+template <> struct WideShape<512> { enum { R0 = 8, R1 = 8, R2 = 8 }; };
+template <> struct WideShape<1024> { enum { R0 = 8, R1 = 8, R2 = 16 }; };
+
+// lanes per line of wide variant v (1: two warps, 2: four warps)
+__host__ __device__ constexpr int wide_tpl(int v) { return v == 2 ? 128 : 64; }
 
 __host__ __device__ constexpr int wpad(int i) { return i + (i >> 5); }
 
-template <int N>
+template <int N, int TPL>
 __host__ __device__ constexpr int wide_line_stride() {
-  return wpad(N + WideShape<N>::TPL + 2) | 1;
+  return wpad(N + TPL + 2) | 1;
 }
 
 // size of the per-pass twiddle table: passes 2 and 3 ([q][k] blocks)
@@ -286,9 +290,9 @@ __host__ __device__ constexpr int wide_tp_size() {
   return WideShape<N>::R0 * WideShape<N>::R1 + WideShape<N>::R0 * WideShape<N>::R1 * WideShape<N>::R2;
 }
 
-template <int N>
+template <int N, int TPL>
 __device__ __forceinline__ int wide_out_pos(int m) {
-  constexpr int H = N / 2, TPL = WideShape<N>::TPL, CH = H / TPL, SBASE = H + TPL - 1;
+  constexpr int H = N / 2, CH = H / TPL, SBASE = H + TPL - 1;
   if (m & 1) {
     const int k = m >> 1;
     return wpad(k + k / CH);
@@ -296,61 +300,66 @@ __device__ __forceinline__ int wide_out_pos(int m) {
   return wpad(SBASE + (m >> 1) - 1);
 }
 
-template <typename T, int N, bool PERM_IN>
+template <typename T, int N, int TPL, bool PERM_IN>
 __device__ __forceinline__ typename C2<T>::t wide_pre_twiddle(const typename C2<T>::t* a, const T* hs, int j) {
   typedef typename C2<T>::t c_t;
   if (j == 0) return mkc<T>((T)0, (T)0);
   const int jm = N - j;
-  const c_t zj = a[PERM_IN ? wide_out_pos<N>(j) : wpad(j)];
-  const c_t zm = a[PERM_IN ? wide_out_pos<N>(jm) : wpad(jm)];
+  const c_t zj = a[PERM_IN ? wide_out_pos<N, TPL>(j) : wpad(j)];
+  const c_t zm = a[PERM_IN ? wide_out_pos<N, TPL>(jm) : wpad(jm)];
   const T h = hs[j < jm ? j : jm];
   const T dx = (zj.x - zm.x) * (T)0.25, dy = (zj.y - zm.y) * (T)0.25;
   return mkc<T>(fma(h, zj.x + zm.x, dx), fma(h, zj.y + zm.y, dy));
 }
 
-template <typename T, int N, int R, int LSP, bool FIRST, bool PERM_IN>
+template <typename T, int N, int TPL, int R, int LSP, bool FIRST, bool PERM_IN>
 __device__ __forceinline__ void wide_pass(typename C2<T>::t* a, int lane, const typename C2<T>::t* tp, const T* hs,
                                           const typename C2<T>::t* tw) {
   typedef typename C2<T>::t c_t;
-  constexpr int TPL = WideShape<N>::TPL, G = N / R, PER = G / TPL;
+  constexpr int G = N / R, PER = (G + TPL - 1) / TPL;
+  constexpr bool FULL = (G % TPL) == 0;
   c_t x[PER][R];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int l = lane + TPL * i;
-    const int k = l & (LSP - 1);
+    if (FULL || l < G) {
+      const int k = l & (LSP - 1);
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int idx = l + q * G;
-      c_t v = FIRST ? wide_pre_twiddle<T, N, PERM_IN>(a, hs, idx) : a[wpad(idx)];
-      if (!FIRST && q > 0) v = cmul<T>(v, tp[q * LSP + k]);
-      x[i][q] = v;
+      for (int q = 0; q < R; ++q) {
+        const int idx = l + q * G;
+        c_t v = FIRST ? wide_pre_twiddle<T, N, TPL, PERM_IN>(a, hs, idx) : a[wpad(idx)];
+        if (!FIRST && q > 0) v = cmul<T>(v, tp[q * LSP + k]);
+        x[i][q] = v;
+      }
+      dft_reg<T, R, N / R>(x[i], tw);
     }
-    dft_reg<T, R, N / R>(x[i], tw);
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int l = lane + TPL * i;
-    const int j = l / LSP, k = l & (LSP - 1);
+    if (FULL || l < G) {
+      const int j = l / LSP, k = l & (LSP - 1);
 #pragma unroll
-    for (int s = 0; s < R; ++s) a[wpad(j * LSP * R + k + s * LSP)] = x[i][s];
+      for (int s = 0; s < R; ++s) a[wpad(j * LSP * R + k + s * LSP)] = x[i][s];
+    }
   }
   __syncthreads();
 }
 
-// Wide-path DST-I of the lines of a CTA (line = threadIdx / 64); every thread
-// of the CTA must call it (CTA-wide barriers).  scratch: 2 complex per line.
-template <typename T, int N, bool PERM_IN>
+// Wide-path DST-I of the lines of a CTA (line = threadIdx / TPL); every thread
+// of the CTA must call it (CTA-wide barriers).  scratch: TPL/32 complex per line.
+template <typename T, int N, int TPL, bool PERM_IN>
 __device__ __forceinline__ void dst_line_wide(typename C2<T>::t* a, int t, const typename C2<T>::t* tw,
                                               const T* hs, const typename C2<T>::t* tp,
                                               typename C2<T>::t* scratch) {
   typedef typename C2<T>::t c_t;
   typedef WideShape<N> S;
-  constexpr int R0 = S::R0, R1 = S::R1, R2 = S::R2, TPL = S::TPL, H = N / 2, CH = H / TPL;
+  constexpr int R0 = S::R0, R1 = S::R1, R2 = S::R2, H = N / 2, CH = H / TPL, NW = TPL / 32;
   constexpr int SBASE = H + TPL - 1;
-  wide_pass<T, N, R0, 1, true, PERM_IN>(a, t, nullptr, hs, tw);
-  wide_pass<T, N, R1, R0, false, false>(a, t, tp, hs, tw);
-  wide_pass<T, N, R2, R0 * R1, false, false>(a, t, tp + R0 * R1, hs, tw);
+  wide_pass<T, N, TPL, R0, 1, true, PERM_IN>(a, t, nullptr, hs, tw);
+  wide_pass<T, N, TPL, R1, R0, false, false>(a, t, tp, hs, tw);
+  wide_pass<T, N, TPL, R2, R0 * R1, false, false>(a, t, tp + R0 * R1, hs, tw);
   // split into C_k (scan layout) and S_k
   c_t cc[CH], ss[CH];
 #pragma unroll
@@ -374,7 +383,7 @@ __device__ __forceinline__ void dst_line_wide(typename C2<T>::t* a, int t, const
     if (k != 0) a[wpad(SBASE + k - 1)] = ss[i];
   }
   __syncthreads();
-  // prefix sum of C: chunk of CH per lane, warp scan, then across the two warps
+  // prefix sum of C: chunk of CH per lane, warp scan, then across the NW warps
   c_t v[CH];
   c_t sum = mkc<T>((T)0, (T)0);
 #pragma unroll
@@ -394,9 +403,11 @@ __device__ __forceinline__ void dst_line_wide(typename C2<T>::t* a, int t, const
     }
   }
   const int line = threadIdx.x / TPL, w = t >> 5;
-  if (lw == 31) scratch[line * 2 + w] = inc;
+  if (lw == 31) scratch[line * NW + w] = inc;
   __syncthreads();
-  if (w == 1) inc = cadd<T>(inc, scratch[line * 2]);
+#pragma unroll
+  for (int u = 0; u < NW - 1; ++u)
+    if (u < w) inc = cadd<T>(inc, scratch[line * NW + u]);
   c_t run = csub<T>(inc, sum);
 #pragma unroll
   for (int i = 0; i < CH; ++i) {
@@ -407,18 +418,19 @@ __device__ __forceinline__ void dst_line_wide(typename C2<T>::t* a, int t, const
 }
 
 // ---------------------------------------------------------------------------
-// One interface for both paths, used by the pass kernels.
+// One interface for the paths, used by the pass kernels.  V = 0: warp per
+// line; V = 1, 2: wide path with 64 or 128 lanes per line.
 //   TPL       lanes per line (lines = threadIdx / TPL)
 //   LS        shared-memory line stride (complex elements)
 //   TP        size of the extra twiddle table (four-step [k1][g] table, or the
 //             wide path's per-pass tables; 0 for single-thread lines)
 //   BLOCK_SYNC whether the transform uses CTA-wide barriers
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool WIDE = (N >= 512)>
+template <typename T, int N, int V = 0>
 struct LineDst;
 
 template <typename T, int N>
-struct LineDst<T, N, false> {
+struct LineDst<T, N, 0> {
   typedef typename C2<T>::t c_t;
   enum { TPL = DstShape<N>::TPL, LS = dst_line_stride<N>(), BLOCK_SYNC = 0,
          TP = DstShape<N>::R2 == 1 ? 0 : N };
@@ -431,22 +443,22 @@ struct LineDst<T, N, false> {
   static __device__ __forceinline__ void line_sync() { __syncwarp(); }
 };
 
-template <typename T, int N>
-struct LineDst<T, N, true> {
+template <typename T, int N, int V>
+struct LineDst {
   typedef typename C2<T>::t c_t;
-  enum { TPL = WideShape<N>::TPL, LS = wide_line_stride<N>(), BLOCK_SYNC = 1, TP = wide_tp_size<N>() };
+  enum { TPL = wide_tpl(V), LS = wide_line_stride<N, wide_tpl(V)>(), BLOCK_SYNC = 1, TP = wide_tp_size<N>() };
   static __device__ __forceinline__ int in_pos(int j) { return wpad(j); }
-  static __device__ __forceinline__ int out_pos(int m) { return wide_out_pos<N>(m); }
+  static __device__ __forceinline__ int out_pos(int m) { return wide_out_pos<N, TPL>(m); }
   template <bool PERM_IN>
   static __device__ __forceinline__ void run(c_t* a, int t, const c_t* tw, const T* hs, const c_t* tp,
                                              c_t* scratch) {
-    dst_line_wide<T, N, PERM_IN>(a, t, tw, hs, tp, scratch);
+    dst_line_wide<T, N, TPL, PERM_IN>(a, t, tw, hs, tp, scratch);
   }
   static __device__ __forceinline__ void line_sync() { __syncthreads(); }
 };
 
 // Host-side size of the extra twiddle table of length N (matches LineDst::TP).
-__host__ __device__ constexpr int line_tp_size(int N, bool wide) {
+__host__ __device__ constexpr int line_tp_size(int N, int wide) {
   return wide ? (N >= 1024 ? wide_tp_size<1024>() : N >= 512 ? wide_tp_size<512>() : 0) : (N >= 64 ? N : 0);
 }
 

@@ -193,6 +193,50 @@ struct StripWindow {
   }
 };
 
+// Operands of one step m of a strip, loaded one step ahead and kept raw (TZ)
+// so that the loads of step m+1 are in flight while step m computes: z at
+// m+1 (the window's next value), the edge lanes' x-neighbours, in 3D the
+// y-neighbours, the diagonal, the faces and v_{j-1}.
+template <int DIM, typename TZ>
+struct StepOperands {
+  TZ zn1, zl, zr, ys, yn;
+  double d, cw, ce, cs, cn, cd, cu;
+  double2 vo;
+  __device__ __forceinline__ void load(const TZ* z, const StencilArgs& a, long p, long mstride, int m, int nm,
+                                       int x, int yfix, bool vx, int lane) {
+    const int nx = a.g.nx, ny = a.g.ny;
+    TZ zero;
+    zero.x = 0;
+    zero.y = 0;
+    zn1 = (vx && m + 1 < nm) ? z[p + mstride] : zero;
+    zl = (lane == 0 && vx && x > 0) ? z[p - 1] : zero;
+    zr = (lane == 31 && x + 1 < nx) ? z[p + 1] : zero;
+    d = cw = ce = cs = cn = cd = cu = 0.0;
+    vo = make_double2(0.0, 0.0);
+    ys = yn = zero;
+    if (vx) {
+      long rx, ry;
+      if (DIM == 2) {
+        rx = (long)m * (nx + 1) + x;
+        ry = (long)m * nx + x;
+      } else {
+        rx = ((long)m * ny + yfix) * (nx + 1) + x;
+        ry = ((long)m * (ny + 1) + yfix) * nx + x;
+        if (yfix > 0) ys = z[p - nx];
+        if (yfix < ny - 1) yn = z[p + nx];
+        cd = a.cz[p];
+        cu = a.cz[p + mstride];
+      }
+      d = a.dg[p];
+      cw = a.cx[rx];
+      ce = a.cx[rx + 1];
+      cs = a.cy[ry];
+      cn = a.cy[ry + nx];
+      vo = a.vold[p];
+    }
+  }
+};
+
 // batch: optional per-system argument array (system = blockIdx.x / bps)
 template <int DIM, typename TZ>
 __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
@@ -206,8 +250,9 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
     if (a.use_cond && bid == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
     return;
   }
+  // z_j arrives normalised (z_j / gamma_j), so A z_j needs no scaling
   const double gam = st->gam, gam_old = st->gam_old, beta = st->beta;
-  const double inv_g = 1.0 / gam, lanc = gam / gam_old;
+  const double lanc = gam / gam_old;
   const int check = st->check;
   const TZ* z = (const TZ*)a.z;
   const int nx = a.g.nx, ny = a.g.ny;
@@ -226,10 +271,57 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
     const bool vx = x < nx;
     const int m0 = sm * kStencilStrip, m1 = min(m0 + kStencilStrip, nm);
     const long base = DIM == 2 ? (long)x : (long)yfix * nx + x;
+    if (!check) {
+      // u' = A z - lanc v_{j-1} and delta, operands of step m+1 loaded
+      // before step m computes
+      const double2 zero = make_double2(0.0, 0.0);
+      double2 zm = (vx && m0 > 0) ? to_d2(z[base + (long)(m0 - 1) * mstride]) : zero;
+      double2 zc = vx ? to_d2(z[base + (long)m0 * mstride]) : zero;
+      StepOperands<DIM, TZ> cur, nxt;
+      cur.load(z, a, base + (long)m0 * mstride, mstride, m0, nm, x, yfix, vx, lane);
+      for (int m = m0; m < m1; ++m) {
+        const long p = base + (long)m * mstride;
+        if (m + 1 < m1) nxt.load(z, a, p + mstride, mstride, m + 1, nm, x, yfix, vx, lane);
+        const double2 zp = to_d2(cur.zn1);
+        double2 zl = shfl_up_d2(zc), zr = shfl_down_d2(zc);
+        if (lane == 0) zl = to_d2(cur.zl);
+        if (lane == 31) zr = to_d2(cur.zr);
+        if (vx) {
+          double ax = cur.d * zc.x, ay = cur.d * zc.y;
+          ax = fma(-cur.cw, zl.x, ax);
+          ay = fma(-cur.cw, zl.y, ay);
+          ax = fma(-cur.ce, zr.x, ax);
+          ay = fma(-cur.ce, zr.y, ay);
+          if (DIM == 2) {
+            ax = fma(-cur.cs, zm.x, ax);
+            ay = fma(-cur.cs, zm.y, ay);
+            ax = fma(-cur.cn, zp.x, ax);
+            ay = fma(-cur.cn, zp.y, ay);
+          } else {
+            const double2 zs = to_d2(cur.ys), zn = to_d2(cur.yn);
+            ax = fma(-cur.cs, zs.x, ax);
+            ay = fma(-cur.cs, zs.y, ay);
+            ax = fma(-cur.cn, zn.x, ax);
+            ay = fma(-cur.cn, zn.y, ay);
+            ax = fma(-cur.cd, zm.x, ax);
+            ay = fma(-cur.cd, zm.y, ay);
+            ax = fma(-cur.cu, zp.x, ax);
+            ay = fma(-cur.cu, zp.y, ay);
+          }
+          const double2 Az = block_A(make_double2(ax, ay), zc, beta);
+          acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
+          a.vold[p] = make_double2(fma(-lanc, cur.vo.x, Az.x), fma(-lanc, cur.vo.y, Az.y));
+        }
+        zm = zc;
+        zc = zp;
+        cur = nxt;
+      }
+      continue;
+    }
     StripWindow<DIM, TZ> wz;
     StripWindow<DIM, double2> wx;
     wz.start(z, base, mstride, m0, vx);
-    if (check) wx.start(a.x, base, mstride, m0, vx);
+    wx.start(a.x, base, mstride, m0, vx);
     for (int m = m0; m < m1; ++m) {
       const long p = base + (long)m * mstride;
       const double2 t = wz.KA(z, a, p, mstride, m, nm, x, yfix, vx, lane);
@@ -240,7 +332,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
         const double2 Az = block_A(t, zc, beta);
         acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
         const double2 vo = a.vold[p];
-        a.vold[p] = make_double2(fma(Az.x, inv_g, -lanc * vo.x), fma(Az.y, inv_g, -lanc * vo.y));
+        a.vold[p] = make_double2(fma(-lanc, vo.x, Az.x), fma(-lanc, vo.y, Az.y));
         if (check) {
           const double2 Ax = block_A(tx, wx.zc, beta);
           const double2 bb = a.b[p];
@@ -256,7 +348,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
   if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
   // scalar step after the stencil: delta_j and the stopping test for x_{iter}
-  st->delta = tot[0] * inv_g * inv_g;
+  st->delta = tot[0];
   if (check) {
     const double rnorm = sqrt(tot[1]);
     const double rel = rnorm / st->bnorm;
@@ -325,7 +417,7 @@ __device__ inline void givens_step(DevState* st, double g2) {
     return;
   }
   const double cn = a0 / a1, sn = gn / a1;
-  st->w_a = 1.0 / (a1 * gam);
+  st->w_a = 1.0 / a1;  // z_j is stored normalised (z_j / gamma_j)
   st->w_b = -a3 / a1;
   st->w_c = -a2 / a1;
   st->x_coef = cn * st->eta;

@@ -6,7 +6,7 @@
 
 namespace csl {
 
-template <typename T, int N, bool W>
+template <typename T, int N, int W>
 cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s,
                          const RowArgs<T>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
@@ -27,22 +27,23 @@ cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLau
 }
 
 template <typename T>
-cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
+cudaError_t launch_row(int N, int wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
                        cudaStream_t s, const RowArgs<T>* batch, int nsys) {
   switch (N) {
 #define CASE(NN)                                                                    \
   case NN:                                                                          \
     if constexpr (NN >= 512) {                                                      \
-      if (wide) return launch_row_n<T, NN, true>(load, store, a, L, s, batch, nsys); \
+      if (wide == 1) return launch_row_n<T, NN, 1>(load, store, a, L, s, batch, nsys); \
+      if (wide == 2) return launch_row_n<T, NN, 2>(load, store, a, L, s, batch, nsys); \
     }                                                                               \
-    return launch_row_n<T, NN, false>(load, store, a, L, s, batch, nsys);
+    return launch_row_n<T, NN, 0>(load, store, a, L, s, batch, nsys);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int N, bool W>
+template <typename T, int N, int W>
 cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s,
                              const StridedArgs<T>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
@@ -54,7 +55,7 @@ cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch
 }
 
 template <typename T>
-cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
+cudaError_t launch_strided(int N, int wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
                            cudaStream_t s, const StridedArgs<T>* batch, int nsys) {
   if constexpr (sizeof(T) == 4) {
     if (L.tc) return launch_strided_tc(N, L.tc, mid, a, L, s, batch, nsys);
@@ -63,9 +64,10 @@ cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, 
 #define CASE(NN)                                                                  \
   case NN:                                                                        \
     if constexpr (NN >= 512) {                                                    \
-      if (wide) return launch_strided_n<T, NN, true>(mid, a, L, s, batch, nsys);  \
+      if (wide == 1) return launch_strided_n<T, NN, 1>(mid, a, L, s, batch, nsys); \
+      if (wide == 2) return launch_strided_n<T, NN, 2>(mid, a, L, s, batch, nsys); \
     }                                                                             \
-    return launch_strided_n<T, NN, false>(mid, a, L, s, batch, nsys);
+    return launch_strided_n<T, NN, 0>(mid, a, L, s, batch, nsys);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -97,19 +99,21 @@ cudaError_t set_pass_attrs() {
   SETA((k_row<T, NN, W, LOAD_T, STORE_D>))             \
   SETA((k_strided<T, NN, W, true>))                    \
   SETA((k_strided<T, NN, W, false>))
-#define CASE(NN) VARIANT(NN, false)
+#define CASE(NN) VARIANT(NN, 0)
   CSL_FOR_EACH_N(CASE)
 #undef CASE
-  VARIANT(512, true)
-  VARIANT(1024, true)
+  VARIANT(512, 1)
+  VARIANT(1024, 1)
+  VARIANT(512, 2)
+  VARIANT(1024, 2)
 #undef VARIANT
 #undef SETA
   return e;
 }
 
-template cudaError_t launch_row<CSL_T>(int, bool, int, int, const RowArgs<CSL_T>&, const PassLaunch&,
+template cudaError_t launch_row<CSL_T>(int, int, int, int, const RowArgs<CSL_T>&, const PassLaunch&,
                                        cudaStream_t, const RowArgs<CSL_T>*, int);
-template cudaError_t launch_strided<CSL_T>(int, bool, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
+template cudaError_t launch_strided<CSL_T>(int, int, bool, const StridedArgs<CSL_T>&, const PassLaunch&,
                                            cudaStream_t, const StridedArgs<CSL_T>*, int);
 template cudaError_t set_pass_attrs<CSL_T>();
 

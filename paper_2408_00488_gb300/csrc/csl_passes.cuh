@@ -20,7 +20,7 @@
 
 // FP32 passes: two CTAs of 256 threads per SM (at most 128 registers per
 // thread); the FP64 lines need the full register file
-#define CSL_PASS_MINB(T) (sizeof(T) == 4 ? 2 : 1)
+#define CSL_PASS_MINB(T, V) (sizeof(T) == 4 ? ((V) == 2 ? 3 : 2) : 1)
 
 namespace csl {
 
@@ -69,22 +69,22 @@ struct StridedArgs {
 
 // byte offsets of the shared-memory regions: twiddles | half sines | extra
 // twiddles | scan scratch (2 per line) | lines
-template <typename T, int N, bool WIDE>
+template <typename T, int N, int WIDE>
 __host__ __device__ constexpr size_t pass_tables_bytes() {
   return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16 +
          (size_t)line_tp_size(N, WIDE) * sizeof(typename C2<T>::t);
 }
-template <typename T, int N, bool WIDE>
+template <typename T, int N, int WIDE>
 __host__ __device__ constexpr size_t pass_smem_bytes(int lines) {
-  return pass_tables_bytes<T, N, WIDE>() + (size_t)lines * 2 * sizeof(typename C2<T>::t) +
+  return pass_tables_bytes<T, N, WIDE>() + (size_t)lines * 4 * sizeof(typename C2<T>::t) +
          (size_t)lines * LineDst<T, N, WIDE>::LS * sizeof(typename C2<T>::t);
 }
 
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
-template <typename T, int N, bool WIDE, int LOAD, int STORE>
-__global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
+template <typename T, int N, int WIDE, int LOAD, int STORE>
+__global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -104,10 +104,14 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_row(RowArgs<T> a0, co
   c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
   const int nlines = blockDim.x / TPL;
   c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
-  c_t* lines = s_scr + 2 * nlines;
+  c_t* lines = s_scr + 4 * nlines;
   load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
   if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
+  // MINRES works with the normalised z_{j+1} / gamma_{j+1}; gamma_{j+1} is
+  // known once the MID pass has run, so the z store applies it
+  T zs = (T)1;
+  if ((STORE == STORE_Z || STORE == STORE_Z_UPDATE) && a.st) zs = (T)(a.st->gam > 0.0 ? 1.0 / a.st->gam : 0.0);
   if (STORE == STORE_Z_UPDATE) {
     wa = a.st->w_a;
     wb = a.st->w_b;
@@ -187,7 +191,8 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_row(RowArgs<T> a0, co
             const int j = t + TPL * (i0 + k);
             if (j < n) {
               const long p = base + j;
-              a.zout[p] = line[D::out_pos(j + 1)];
+              const c_t F = line[D::out_pos(j + 1)];
+              a.zout[p] = mkc<T>(F.x * zs, F.y * zs);
               const double2 zd = to_d2(zo[k]);
               const double2 wn = make_double2(fma(wa, zd.x, fma(wb, wp[k].x, wc * wq[k].x)),
                                               fma(wa, zd.y, fma(wb, wp[k].y, wc * wq[k].y)));
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_row(RowArgs<T> a0, co
               else if (STORE == STORE_D)
                 a.dout[p] = to_d2(F);
               else
-                a.zout[p] = F;
+                a.zout[p] = mkc<T>(F.x * zs, F.y * zs);
             }
           }
         }
@@ -245,8 +250,8 @@ __device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, 
   givens_step(st, tot[0]);
 }
 
-template <typename T, int N, bool WIDE, bool MID>
-__global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
+template <typename T, int N, int WIDE, bool MID>
+__global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T)) k_strided(StridedArgs<T
   c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
   const int C = blockDim.x / TPL;  // lines (columns) per tile, a power of two
   c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
-  c_t* lines = s_scr + 2 * C;
+  c_t* lines = s_scr + 4 * C;
   load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
   int logC = 0;
   while ((1 << logC) < C) ++logC;
@@ -345,19 +350,21 @@ struct PassLaunch {
 
 #define CSL_FOR_EACH_N(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
-// N = 512 and 1024 exist in both variants (warp-per-line four-step and the
-// two-warp Stockham path); the autotuner picks one per pass.
+// N = 512 and 1024 exist in three variants (warp per line, 64 and 128 lanes
+// per line: wide = 0, 1, 2); the autotuner picks one per pass.
 inline bool pass_has_wide(int N) { return N == 512 || N == 1024; }
+inline int pass_num_variants(int N) { return pass_has_wide(N) ? 3 : 1; }
 
 template <typename T>
-size_t pass_smem(int N, bool wide, int lines) {
+size_t pass_smem(int N, int wide, int lines) {
   switch (N) {
 #define CASE(NN)                                                                       \
   case NN:                                                                             \
     if constexpr (NN >= 512) {                                                         \
-      if (wide) return pass_smem_bytes<T, NN, true>(lines);                            \
+      if (wide == 1) return pass_smem_bytes<T, NN, 1>(lines);                          \
+      if (wide == 2) return pass_smem_bytes<T, NN, 2>(lines);                          \
     }                                                                                  \
-    return pass_smem_bytes<T, NN, false>(lines);
+    return pass_smem_bytes<T, NN, 0>(lines);
     CSL_FOR_EACH_N(CASE)
 #undef CASE
   }
@@ -365,14 +372,15 @@ size_t pass_smem(int N, bool wide, int lines) {
 }
 
 template <int NN>
-inline int pass_tpl_n(bool wide) {
+inline int pass_tpl_n(int wide) {
   if constexpr (NN >= 512) {
-    if (wide) return LineDst<float, NN, true>::TPL;
+    if (wide == 1) return LineDst<float, NN, 1>::TPL;
+    if (wide == 2) return LineDst<float, NN, 2>::TPL;
   }
-  return LineDst<float, NN, false>::TPL;
+  return LineDst<float, NN, 0>::TPL;
 }
 
-inline int pass_tpl(int N, bool wide) {
+inline int pass_tpl(int N, int wide) {
   switch (N) {
 #define CASE(NN) \
   case NN: return pass_tpl_n<NN>(wide);
@@ -385,10 +393,10 @@ inline int pass_tpl(int N, bool wide) {
 // batch (optional): device array of per-system arguments; the grid is then
 // L.blocks blocks per system times nsys
 template <typename T>
-cudaError_t launch_row(int N, bool wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
+cudaError_t launch_row(int N, int wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
                        cudaStream_t s, const RowArgs<T>* batch = nullptr, int nsys = 0);
 template <typename T>
-cudaError_t launch_strided(int N, bool wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
+cudaError_t launch_strided(int N, int wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
                            cudaStream_t s, const StridedArgs<T>* batch = nullptr, int nsys = 0);
 template <typename T>
 cudaError_t set_pass_attrs();

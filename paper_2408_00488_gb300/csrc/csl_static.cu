@@ -166,7 +166,7 @@ void setup_device(int dev) {
 // CTA shape of one pass (same rules as the plan's default configuration)
 template <typename T>
 PassLaunch static_launch(int N, long nlines_or_tiles_per_cta_unit, bool strided, int ncols, int nouter) {
-  const bool wide = pass_has_wide(N);
+  const int wide = pass_has_wide(N) ? 1 : 0;
   const int tpl = pass_tpl(N, wide);
   int threads = 256;
   if (strided)
@@ -215,7 +215,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
   r1.vin = v;
   r1.tout = Tbuf;
   const PassLaunch Lr = static_launch<T>(nx + 1, M / nx, false, 0, 0);
-  e = launch_row<T>(nx + 1, pass_has_wide(nx + 1), LOAD_V, STORE_T, r1, Lr, s);
+  e = launch_row<T>(nx + 1, pass_has_wide(nx + 1) ? 1 : 0, LOAD_V, STORE_T, r1, Lr, s);
   if (e != cudaSuccess) return e;
   auto strided = [&](int axis, int nn, int nouter, long outer_stride, long line_stride, bool mid) {
     StridedArgs<T> a;
@@ -243,7 +243,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
       a.cnorm = (T)cnorm;
     }
     const PassLaunch L = static_launch<T>(nn + 1, 0, true, nx, nouter);
-    return launch_strided<T>(nn + 1, pass_has_wide(nn + 1), mid, a, L, s);
+    return launch_strided<T>(nn + 1, pass_has_wide(nn + 1) ? 1 : 0, mid, a, L, s);
   };
   if (dim == 2) {
     e = strided(1, ny, 1, 0, nx, true);
@@ -258,7 +258,7 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
   r3.tout = nullptr;
   r3.tin = Tbuf;
   r3.dout = out;
-  return launch_row<T>(nx + 1, pass_has_wide(nx + 1), LOAD_T, STORE_D, r3, Lr, s);
+  return launch_row<T>(nx + 1, pass_has_wide(nx + 1) ? 1 : 0, LOAD_T, STORE_D, r3, Lr, s);
 }
 
 }  // namespace
