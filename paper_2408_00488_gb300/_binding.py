@@ -37,6 +37,8 @@ class SystemDesc(ctypes.Structure):
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _SIGS = {
+    "csl_test_convert_d2f": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "csl_test_convert_f2d": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "csl_version": (ctypes.c_char_p, []),
     "csl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "csl_last_error": (ctypes.c_char_p, []),
@@ -376,3 +378,21 @@ def precondition_static(v, gamma: float, lam: complex, precision: str = "fp64", 
                                      _stream_handle(stream))
     _check(st, "csl_precondition_static")
     return y
+
+
+def test_convert(x, out_dtype, stream=None):
+    """Test hook (include/csl_testing.h): the FP32-form kernels' integer-field
+    conversion of a float64 CUDA tensor to float32 (round to nearest even) or
+    of a float32 tensor to float64."""
+    torch = _torch()
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    if x.dtype == torch.float64 and out_dtype == torch.float32:
+        st = lib.csl_test_convert_d2f(x.data_ptr(), out.data_ptr(), x.numel(), _stream_handle(stream))
+    elif x.dtype == torch.float32 and out_dtype == torch.float64:
+        st = lib.csl_test_convert_f2d(x.data_ptr(), out.data_ptr(), x.numel(), _stream_handle(stream))
+    else:
+        raise ValueError("float64 -> float32 or float32 -> float64")
+    _check(st, "csl_test_convert")
+    return out
+

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/csl.h"
+#include "../../include/csl_testing.h"
 #include "csl_kernels.cuh"
 #include "csl_passes.cuh"
 
@@ -525,6 +526,7 @@ cudaError_t autotune(csl_plan* P) {
   DevState h;
   memset(&h, 0, sizeof(h));
   h.gam = h.gam_old = h.gam1 = 1.0;
+  h.a1_old = h.a1_old2 = 1.0;
   h.c = h.c_old = 1.0;
   h.eta = h.eta_x = h.bnorm = 1.0;
   h.tol = 1e-300;
@@ -1081,6 +1083,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   DevState h;
   memset(&h, 0, sizeof(h));
   h.gam = h.gam_old = h.gam1 = 1.0;
+  h.a1_old = h.a1_old2 = 1.0;
   h.c = h.c_old = 1.0;
   h.eta = h.eta_x = h.bnorm = 1.0;
   h.tol = 1e-300;
@@ -1634,3 +1637,42 @@ size_t csl_batch_workspace_bytes(const csl_batch* B) {
 }
 
 }  // extern "C"
+
+// ---- test hooks (include/csl_testing.h) -------------------------------------
+namespace {
+__global__ void k_test_d2f(const double* in, float* out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = csl::d2f_rn(in[i]);
+}
+__global__ void k_test_f2d(const float* in, double* out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = csl::f2d_exact(in[i]);
+}
+}  // namespace
+
+csl_status csl_test_convert_d2f(const double* in, float* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!in || !out))) return CSL_INVALID_ARG;
+  if (n == 0) return CSL_OK;
+  const long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_test_d2f<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(in, out, (long)n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    CSL_NOTE(e, "csl_test_convert_d2f");
+    return CSL_CUDA_ERROR;
+  }
+  return CSL_OK;
+}
+
+csl_status csl_test_convert_f2d(const float* in, double* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!in || !out))) return CSL_INVALID_ARG;
+  if (n == 0) return CSL_OK;
+  const long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_test_f2d<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(in, out, (long)n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    CSL_NOTE(e, "csl_test_convert_f2d");
+    return CSL_CUDA_ERROR;
+  }
+  return CSL_OK;
+}
+

@@ -39,17 +39,34 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// Double -> float with round-to-nearest-even by integer field moves, for the
+// same reason (the hardware conversion issues on the FP64 pipe): the 52-bit
+// mantissa is cut to 23 bits and rounded up when the 29 dropped bits exceed
+// half an ulp, or equal it with an odd kept mantissa; a carry out of the
+// mantissa increments the exponent (and overflows to infinity at the top).
+// Results that would be zero or subnormal, and infinities / NaN, take the
+// hardware path.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(d);  // float exponent 1..254 only
+  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f);
+}
+
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(f2d_exact(v.x), f2d_exact(v.y)); }
 template <typename T> __device__ __forceinline__ typename C2<T>::t from_d2(double2 v);
 template <> __device__ __forceinline__ double2 from_d2<double>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 from_d2<float>(double2 v) {
-  return make_float2((float)v.x, (float)v.y);
+  return make_float2(d2f_rn(v.x), d2f_rn(v.y));
 }
 template <typename TZ> __device__ __forceinline__ TZ store_as(double2 v);
 template <> __device__ __forceinline__ double2 store_as<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 store_as<float2>(double2 v) {
-  return make_float2((float)v.x, (float)v.y);
+  return make_float2(d2f_rn(v.x), d2f_rn(v.y));
 }
 
 // Scalars of one MINRES solve, resident in device memory so that the whole
@@ -60,8 +77,10 @@ struct DevState {
   double gam, gam_old, gam1, delta;
   // Givens rotations (c_j, c_{j-1}, s_j, s_{j-1}) and the rotated right-hand side eta
   double c, c_old, s, s_old, eta;
-  // coefficients of the fused update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1}
-  double w_a, w_b, w_c, x_coef;
+  // coefficients of the fused update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1};
+  // the w vectors are kept scaled by the a1 of the step that made them
+  // (w_a = 1), a1_old / a1_old2 being those of the last two steps
+  double w_a, w_b, w_c, x_coef, a1_old, a1_old2;
   double bnorm, tol;
   double rho;     // calibrated ratio ||b - A x||_2 / |eta| (residual 2-norm per P^{-1}-norm)
   double relres;  // last explicitly evaluated true relative residual

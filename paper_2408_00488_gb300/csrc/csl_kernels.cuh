@@ -417,10 +417,16 @@ __device__ inline void givens_step(DevState* st, double g2) {
     return;
   }
   const double cn = a0 / a1, sn = gn / a1;
-  st->w_a = 1.0 / a1;  // z_j is stored normalised (z_j / gamma_j)
-  st->w_b = -a3 / a1;
-  st->w_c = -a2 / a1;
-  st->x_coef = cn * st->eta;
+  // w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j) / a1 with z_j stored normalised
+  // (z_j / gamma_j); the buffers hold w_k scaled by the a1 that made it, so
+  // that the update needs no product with z: a1 w_{j+1} = z_j - (a3/a1'') (a1'' w_{j-1})
+  // - (a2/a1') (a1' w_j), and x += (c_{j+1} eta / a1) (a1 w_{j+1})
+  st->w_a = 1.0;
+  st->w_b = -a3 / st->a1_old2;
+  st->w_c = -a2 / st->a1_old;
+  st->x_coef = cn * st->eta / a1;
+  st->a1_old2 = st->a1_old;
+  st->a1_old = a1;
   st->eta = -sn * st->eta;
   st->c_old = c;
   st->c = cn;
@@ -494,6 +500,7 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const Inge
   st->s = st->s_old = 0.0;
   st->delta = 0.0;
   st->gam = st->gam_old = st->gam1 = 1.0;
+  st->a1_old = st->a1_old2 = 1.0;
   st->eta = st->eta_x = 0.0;
   st->rho = 0.0;
   st->iter = 0;

@@ -106,14 +106,13 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> 
   c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
   c_t* lines = s_scr + 4 * nlines;
   load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
-  double lz = 0.0, wa = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
+  double lz = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
   if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
   // MINRES works with the normalised z_{j+1} / gamma_{j+1}; gamma_{j+1} is
   // known once the MID pass has run, so the z store applies it
   T zs = (T)1;
   if ((STORE == STORE_Z || STORE == STORE_Z_UPDATE) && a.st) zs = (T)(a.st->gam > 0.0 ? 1.0 / a.st->gam : 0.0);
   if (STORE == STORE_Z_UPDATE) {
-    wa = a.st->w_a;
     wb = a.st->w_b;
     wc = a.st->w_c;
     xc = a.st->x_coef;
@@ -194,8 +193,9 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> 
               const c_t F = line[D::out_pos(j + 1)];
               a.zout[p] = mkc<T>(F.x * zs, F.y * zs);
               const double2 zd = to_d2(zo[k]);
-              const double2 wn = make_double2(fma(wa, zd.x, fma(wb, wp[k].x, wc * wq[k].x)),
-                                              fma(wa, zd.y, fma(wb, wp[k].y, wc * wq[k].y)));
+              // scaled w: w_a = 1 (see givens_step)
+              const double2 wn = make_double2(fma(wb, wp[k].x, fma(wc, wq[k].x, zd.x)),
+                                              fma(wb, wp[k].y, fma(wc, wq[k].y, zd.y)));
               a.wprev[p] = wn;
               a.x[p] = make_double2(fma(xc, wn.x, xo[k].x), fma(xc, wn.y, xo[k].y));
             }

@@ -1,5 +1,5 @@
 """CPU tests of the C-ABI library: it loads without a GPU, exports every
-function include/csl.h declares, and rejects bad arguments on the host."""
+function include/*.h declares, and rejects bad arguments on the host."""
 import ctypes
 import os
 import re
@@ -7,7 +7,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "csl.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +20,7 @@ def csl():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s*(csl_\w+)\s*\(", text, flags=re.M)))
 
