@@ -26,6 +26,12 @@ textbook preconditioned MINRES recurrence.  Function by function:
   matrix_abs / theorem helpers
                      the definitions of |H| and sqrt(H) (Section 1) and the
                      bounds of Theorem 2.3 / 2.4, for invariant tests.
+  paradiag_*         the all-at-once time solve that motivates the shifted
+                     systems (Section 1): backward Euler for u' + K u = g as
+                     one block system, the alpha-circulant approximation of
+                     its time matrix, its diagonalisation by the DFT in time
+                     into complex-shifted Laplacian systems, and the
+                     preconditioned Richardson iteration built on them.
 
 Readings where the paper is silent or garbled (each is also listed in the
 design notes): unit square/cube with homogeneous Dirichlet data and
@@ -484,3 +490,96 @@ def theorem24_factor(amin: float, amax: float, c0: float, alpha: float, beta: fl
         mu0sq = hi * hi
         return (mu0sq - 1.0) / (mu0sq + 1.0)
     return (hi - lo) / (hi + lo)
+
+
+# ---------------------------------------------------------------------------
+# All-at-once time solve (Section 1: triangular time-discretisation matrices
+# approximated by alpha-circulant ones, block-diagonalised into
+# complex-shifted Laplacian systems).  Backward Euler for u' + K u = g on
+# L steps of size tau:
+#     (B kron I + I kron K) U = F,  B = (I - S)/tau  (S: ones on the subdiagonal),
+#     F_0 = g_0 + u_0 / tau,  F_n = g_n  (n >= 1).
+# alpha-circulant approximation: C_a = (I - S_a)/tau, S_a = S plus a at (0, L-1).
+# With Gam = diag(a^{-j/L}) and the DFT matrix Fd[k, j] = exp(-2 pi i j k / L),
+#     C_a = Gam Fd^{-1} diag(d_k) Fd Gam^{-1},  d_k = (1 - a^{1/L} exp(-2 pi i k/L)) / tau,
+# so P_a = C_a kron I + I kron K is inverted by a scaled DFT in time, L
+# shifted solves (d_k I + K) Z_k = R_k, and the inverse.
+# ---------------------------------------------------------------------------
+def paradiag_time_matrix(L: int, tau: float) -> np.ndarray:
+    """B = (I - S)/tau, the backward-Euler time matrix (dense, L x L)."""
+    return (np.eye(L) - np.eye(L, k=-1)) / tau
+
+
+def paradiag_circulant(L: int, tau: float, a: float) -> np.ndarray:
+    """C_a = (I - S_a)/tau: B with a in the top-right corner of the shift."""
+    S = np.eye(L, k=-1)
+    S[0, L - 1] = a
+    return (np.eye(L) - S) / tau
+
+
+def paradiag_shifts(L: int, tau: float, a: float) -> np.ndarray:
+    """d_k = (1 - a^{1/L} exp(-2 pi i k/L)) / tau, the eigenvalues of C_a."""
+    k = np.arange(L)
+    return (1.0 - a ** (1.0 / L) * np.exp(-2j * np.pi * k / L)) / tau
+
+
+def paradiag_apply(faces, tau: float, U: np.ndarray) -> np.ndarray:
+    """(B kron I + I kron K) U for U of shape (L, *grid): time slices first."""
+    out = np.empty_like(U, dtype=np.complex128)
+    for n in range(U.shape[0]):
+        out[n] = apply_K(faces, U[n]) + U[n] / tau
+        if n > 0:
+            out[n] -= U[n - 1] / tau
+    return out
+
+
+def paradiag_rhs(tau: float, u0: np.ndarray, g: np.ndarray) -> np.ndarray:
+    F = np.array(g, dtype=np.complex128)
+    F[0] = F[0] + u0 / tau
+    return F
+
+
+def paradiag_time_stepping(faces, tau: float, u0: np.ndarray, g: np.ndarray, tol: float = 1e-13,
+                           maxit: int = 2000) -> np.ndarray:
+    """The exact all-at-once solution by sequential backward Euler:
+    (K + I/tau) u_n = g_n + u_{n-1}/tau, each step solved with `solve`."""
+    U = np.empty(np.shape(g), dtype=np.complex128)
+    prev = np.asarray(u0, dtype=np.complex128)
+    for n in range(U.shape[0]):
+        U[n], _ = solve(faces, 1.0 / tau, g[n] + prev / tau, tol, maxit)
+        prev = U[n]
+    return U
+
+
+def paradiag_precond(faces, tau: float, a: float, R: np.ndarray, tol: float = 1e-12, maxit: int = 2000):
+    """P_a^{-1} R: R_hat = Fd Gam^{-1} R (time slice j scaled by a^{j/L}, then
+    the DFT over the slices), Z_k = (d_k I + K)^{-1} R_hat_k, Z = Gam Fd^{-1} Z_hat."""
+    L = R.shape[0]
+    j = np.arange(L).reshape((L,) + (1,) * (R.ndim - 1))
+    Fd = np.exp(-2j * np.pi * np.outer(np.arange(L), np.arange(L)) / L)
+    Rh = np.tensordot(Fd, (a ** (j / L)) * R, axes=(1, 0))
+    d = paradiag_shifts(L, tau, a)
+    Zh = np.empty_like(Rh)
+    for k in range(L):
+        Zh[k], _ = solve(faces, d[k], Rh[k], tol, maxit)
+    Z = np.tensordot(np.conj(Fd) / L, Zh, axes=(1, 0))
+    return (a ** (-j / L)) * Z
+
+
+def paradiag_solve(faces, tau: float, a: float, u0: np.ndarray, g: np.ndarray, tol: float = 1e-10,
+                   maxit: int = 20, inner_tol: float = 1e-12):
+    """Preconditioned Richardson on the all-at-once system, U_0 = 0,
+    U <- U + P_a^{-1}(F - A U), stopping when ||F - A U|| <= tol ||F||.
+    Returns (U, list of relative residual norms before each update)."""
+    F = paradiag_rhs(tau, u0, g)
+    U = np.zeros_like(F)
+    fn = np.linalg.norm(F)
+    hist = []
+    for _ in range(maxit + 1):
+        R = F - paradiag_apply(faces, tau, U)
+        hist.append(float(np.linalg.norm(R) / fn))
+        if hist[-1] <= tol or len(hist) > maxit:
+            break
+        U = U + paradiag_precond(faces, tau, a, R, inner_tol)
+    return U, hist
+
