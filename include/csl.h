@@ -127,6 +127,41 @@ void csl_plan_destroy(csl_plan* plan);
 csl_status csl_plan_set_stream(csl_plan* plan, void* stream);
 
 /* Device bytes owned by the plan. */
+/*
+ * All-at-once time solve (the setting Section 1 gives for the shifted
+ * systems; a growth row of this library, not an algorithm of the paper).
+ * Backward Euler for u' + K u = g on L steps of size tau,
+ *     (B kron I + I kron K) U = F,  B = (I - S)/tau (S: ones on the subdiagonal),
+ *     F_0 = g_0 + u0/tau,  F_n = g_n,
+ * solved by preconditioned Richardson U <- U + P_a^{-1} (F - A U), U_0 = 0,
+ * with the alpha-circulant P_a = C_a kron I + I kron K, C_a = (I - S_a)/tau
+ * (S with a in its top-right corner).  P_a^{-1} is a DFT in time of the
+ * slices scaled by a^{j/L}, the L complex-shifted solves
+ * (d_k I + K) Z_k = R_k, d_k = (1 - a^{1/L} e^{-2 pi i k/L}) / tau, in one
+ * batch (csl_batch_*), and the inverse DFT scaled by a^{-j/L}.  The sweep
+ * count falls roughly like a^s.
+ *
+ * L must be a power of two in [2, 1024] (else CSL_UNSUPPORTED_SIZE), 0 < a < 1,
+ * tau > 0.  Slices are stored slice-major (slice j of point p at j*M + p),
+ * complex128, DEVICE pointers: u0 has M entries, g and u have L*M.  opt (may
+ * be NULL) applies to the L shifted solves.  Stream-ordered on `stream`; the
+ * solve synchronises it once per sweep (to read the residual norm).
+ */
+typedef struct csl_paradiag csl_paradiag;
+typedef struct csl_paradiag_info {
+  int sweeps;           /* P_a^{-1} applications                                     */
+  int status;           /* CSL_OK when relres <= tol, else CSL_NOT_CONVERGED / error */
+  double relres;        /* ||F - A U||_2 / ||F||_2 of the returned U                  */
+  int inner_iters_max;  /* largest MINRES iteration count among the shifted solves    */
+  int reserved[5];
+} csl_paradiag_info;
+
+csl_status csl_paradiag_create(csl_paradiag** out, int dim, const int64_t n[3], const double* const coef_faces[3],
+                               int L, double tau, double a, const csl_plan_options* opt, void* stream);
+csl_status csl_paradiag_solve(csl_paradiag* pd, const double* u0, const double* g, double* u, double tol,
+                              int maxit, double inner_tol, int inner_maxit, csl_paradiag_info* info);
+void csl_paradiag_destroy(csl_paradiag* pd);
+
 size_t csl_plan_workspace_bytes(const csl_plan* plan);
 
 /* Human-readable launch configuration the plan chose (autotuned or default). */

@@ -36,7 +36,18 @@ class SystemDesc(ctypes.Structure):
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
+class ParaDiagInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double),
+                ("inner_iters_max", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
 _SIGS = {
+    "csl_paradiag_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(PlanOptions), _P]),
+    "csl_paradiag_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int, ctypes.POINTER(ParaDiagInfo)]),
+    "csl_paradiag_destroy": (None, [_P]),
     "csl_test_convert_d2f": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "csl_test_convert_f2d": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "csl_version": (ctypes.c_char_p, []),
@@ -395,4 +406,60 @@ def test_convert(x, out_dtype, stream=None):
         raise ValueError("float64 -> float32 or float32 -> float64")
     _check(st, "csl_test_convert")
     return out
+
+
+class ParaDiag:
+    """All-at-once backward-Euler solve of u' + K u = g on L steps of size tau
+    (csl_paradiag_*): preconditioned Richardson with the alpha-circulant time
+    matrix, whose P^{-1} is a DFT in time plus L batched complex-shifted
+    solves.  faces as for Plan; u0 a complex128 grid tensor, g a complex128
+    tensor of shape (L, *grid)."""
+
+    def __init__(self, faces, L: int, tau: float, a: float, precision: str = "fp64", autotune: bool = True,
+                 stream=None):
+        faces = [f.contiguous() for f in faces]
+        dim = len(faces)
+        nx = faces[0].shape[-1] - 1
+        ny = faces[0].shape[-2]
+        nz = faces[0].shape[-3] if dim == 3 else 1
+        self.shape = (ny, nx) if dim == 2 else (nz, ny, nx)
+        self.L = int(L)
+        n = (ctypes.c_int64 * 3)(nx, ny, nz)
+        fp = (_P * 3)(*[_dptr(faces[d], ("float64",), "faces") if d < dim else None for d in range(3)])
+        opt = PlanOptions()
+        lib.csl_plan_options_init(ctypes.byref(opt))
+        opt.precision = _PREC[precision]
+        opt.autotune = 1 if autotune else 0
+        h = _P()
+        _check(lib.csl_paradiag_create(ctypes.byref(h), dim, n, fp, self.L, float(tau), float(a), ctypes.byref(opt),
+                                       _stream_handle(stream)), "csl_paradiag_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.csl_paradiag_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, u0, g, tol: float = 1e-10, maxit: int = 20, inner_tol: float = 1e-12, inner_maxit: int = 2000,
+              out=None):
+        torch = _torch()
+        u = torch.empty_like(g) if out is None else out
+        info = ParaDiagInfo()
+        st = lib.csl_paradiag_solve(self._h, _dptr(u0.contiguous(), ("complex128",), "u0"),
+                                    _dptr(g.contiguous(), ("complex128",), "g"), _dptr(u, ("complex128",), "u"),
+                                    float(tol), int(maxit), float(inner_tol), int(inner_maxit), ctypes.byref(info))
+        _check(st, "csl_paradiag_solve", allow=(OK, NOT_CONVERGED))
+        return u, info
 
