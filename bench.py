@@ -330,6 +330,7 @@ def main():
                     help="host-driven iteration loop (every kernel a separate launch, for launch lists)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched config-3 line")
     ap.add_argument("--no-config2", action="store_true", help="skip the config-2 forms (FFT vs tensor-core DST)")
+    ap.add_argument("--no-paradiag", action="store_true", help="skip the all-at-once time-solve line")
     ap.add_argument("--profile", choices=["config1", "config2"], default=None,
                     help="solve once, then launch each kernel of one MINRES iteration inside an "
                          "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32 "
@@ -509,6 +510,41 @@ def main():
                           "kernels_us": {k: round(ms * 1e3, 1) for k, ms in kt}, "plan": p2.config}
             p2.close()
 
+    # ---- all-at-once backward Euler (csl_paradiag): the config-3 setting ----
+    pdline = None
+    if not args.no_paradiag:
+        n3, L3, a3 = 127, 64, 1e-4
+        tau3 = 1.0 / L3
+        fc3 = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in W.sample_faces(2, n3, W.coef_c0)]
+        u0 = torch.from_numpy(W.rhs_uniform((n3, n3), 62)).to(dev)
+        g3 = torch.from_numpy(W.rhs_normal((L3, n3, n3), 63) * 0.1).to(dev)
+        pd = csl.ParaDiag(fc3, L3, tau3, a3, precision="fp32")
+        for _ in range(2):
+            pd.solve(u0, g3, tol=1e-10, maxit=10, inner_tol=1e-10)
+        barrier()
+        ms_pd, pinfo = timed(lambda: pd.solve(u0, g3, tol=1e-10, maxit=10, inner_tol=1e-10)[1],
+                             max(3, args.steps // 2), "timed_paradiag")
+        barrier()
+        ms_pd = max_over_ranks(ms_pd)
+        assert pinfo.status == 0 and pinfo.relres <= 1e-10
+        pd.close()
+        # one implicit step (K + I/tau) u = rhs at the same accuracy: L of them,
+        # one after the other, are what sequential time stepping costs
+        ps = csl.Plan(fc3, 1.0 / tau3, precision="fp32")
+        rhs = g3[0].contiguous()
+        for _ in range(2):
+            ps.solve(rhs, tol=1e-10, maxit=MAXIT)
+        ms_step, sinfo = timed(lambda: ps.solve(rhs, tol=1e-10, maxit=MAXIT)[1], max(3, args.steps // 2),
+                               "timed_step")
+        ps.close()
+        pdline = {"workload": f"backward Euler u' + K u = g on [0,1], 2D n={n3} (a as config 0), L={L3} steps, "
+                              f"alpha-circulant a={a3}; u0 ~ U[-1,1]^2 seed 62, g ~ 0.1 N(0,1)^2 seed 63; "
+                              f"tol 1e-10 on the all-at-once residual",
+                  "ms_per_solve": ms_pd, "time_steps_per_s": job_rate(L3, world, ms_pd), "sweeps": pinfo.sweeps,
+                  "relres": pinfo.relres, "inner_iters_max": pinfo.inner_iters_max,
+                  "sequential_estimate_ms": L3 * ms_step, "step_iters": sinfo.iters,
+                  "speedup_vs_sequential": L3 * ms_step / ms_pd}
+
     # ---- CPU baseline: the oracle on a bounded sample ----------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -534,6 +570,7 @@ def main():
             "solve_hbm_frac": round(hbm_pct_solve, 4),
             "batched": batched,
             "config2_forms": cfg2,
+            "paradiag": pdline,
             "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
