@@ -26,6 +26,10 @@ textbook preconditioned MINRES recurrence.  Function by function:
   matrix_abs / theorem helpers
                      the definitions of |H| and sqrt(H) (Section 1) and the
                      bounds of Theorem 2.3 / 2.4, for invariant tests.
+  helmholtz_fgmres   the other setting of Section 1: the shifted system as
+                     the (shifted-Laplace) preconditioner of an outer
+                     Krylov solve of (K + lambda_A I) u = f, lambda_A = -k^2
+                     (flexible GMRES, right preconditioning).
   paradiag_*         the all-at-once time solve that motivates the shifted
                      systems (Section 1): backward Euler for u' + K u = g as
                      one block system, the alpha-circulant approximation of
@@ -582,4 +586,72 @@ def paradiag_solve(faces, tau: float, a: float, u0: np.ndarray, g: np.ndarray, t
             break
         U = U + paradiag_precond(faces, tau, a, R, inner_tol)
     return U, hist
+
+
+# ---------------------------------------------------------------------------
+# Shifted-Laplace preconditioning of an outer Krylov solve (Section 1: the
+# complex-shifted Laplacian "was initially introduced as a preconditioner"
+# for Helmholtz problems).  Restarted flexible GMRES (right preconditioning)
+# for (K + lam_A I) u = f, with z_j = M^{-1} v_j given by `solve` on
+# (K + lam_M I) to a relative residual inner_tol.  Arnoldi with two passes of
+# classical Gram-Schmidt; complex inner product <v, w> = sum conj(v) w.
+# ---------------------------------------------------------------------------
+def helmholtz_fgmres(faces, lam_A: complex, lam_M: complex, f: np.ndarray, tol: float = 1e-8,
+                     maxit: int = 200, restart: int = 30, inner_tol: float = 1e-6, inner_maxit: int = 2000):
+    """Returns (u, info dict: iters, relres history of the Arnoldi estimate,
+    final true relres)."""
+    f = np.asarray(f, dtype=np.complex128)
+    fn = np.linalg.norm(f)
+    x = np.zeros_like(f)
+    A = lambda u: apply_K(faces, u) + lam_A * u
+    iters = 0
+    hist = []
+    while True:
+        r = f - A(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * fn or iters >= maxit:
+            break
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        g[0] = beta
+        cs = np.zeros(restart, dtype=np.complex128)
+        sn = np.zeros(restart, dtype=np.complex128)
+        jdone = 0
+        for j in range(restart):
+            z, _ = solve(faces, lam_M, V[j], inner_tol, inner_maxit)
+            Z.append(z)
+            w = A(z)
+            for _pass in range(2):
+                for i in range(j + 1):
+                    hij = np.vdot(V[i], w)
+                    H[i, j] += hij
+                    w = w - hij * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j] if H[j + 1, j] != 0 else w)
+            # Givens rotations on the new column: with c = a/rho, s = b/rho,
+            # (top, bottom) -> (conj(c) top + conj(s) bottom, -s top + c bottom)
+            for i in range(j):
+                t = np.conj(cs[i]) * H[i, j] + np.conj(sn[i]) * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            a_, b_ = H[j, j], H[j + 1, j]
+            den = math.sqrt(abs(a_) ** 2 + abs(b_) ** 2)
+            cs[j] = a_ / den if den != 0 else 1.0
+            sn[j] = b_ / den if den != 0 else 0.0
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = np.conj(cs[j]) * g[j]
+            iters += 1
+            jdone = j + 1
+            hist.append(float(abs(g[j + 1]) / fn))
+            if hist[-1] <= tol or iters >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:jdone, :jdone]), g[:jdone])
+        for i in range(jdone):
+            x = x + y[i] * Z[i]
+    rel = float(np.linalg.norm(f - A(x)) / fn)
+    return x, {"iters": iters, "hist": hist, "relres": rel}
 
