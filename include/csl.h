@@ -162,6 +162,37 @@ csl_status csl_paradiag_solve(csl_paradiag* pd, const double* u0, const double* 
                               int maxit, double inner_tol, int inner_maxit, csl_paradiag_info* info);
 void csl_paradiag_destroy(csl_paradiag* pd);
 
+/*
+ * The shifted system as a preconditioner (Section 1: the complex-shifted
+ * Laplacian was introduced as the "shifted Laplace" preconditioner of
+ * Helmholtz problems; a growth row of this library, not an algorithm of the
+ * paper).  Restarted flexible GMRES for (K + lam_A I) u = f (e.g. lam_A = -k^2),
+ * right-preconditioned by z = M^{-1} v with M = K + lam_M I (e.g.
+ * lam_M = -k^2 (1 - 0.5 i)), each application one csl_solve to the relative
+ * residual inner_tol (inexact solves are allowed: the flexible variant keeps
+ * the preconditioned vectors).  restart in [1, 200]; lam_M must give a
+ * nonsingular P (as csl_plan_create).  f, u: complex128 DEVICE vectors of M
+ * entries.  Stops when ||f - (K + lam_A I) u|| <= tol ||f|| (true residual,
+ * checked at every restart) or after maxit Arnoldi steps; u = 0 initially.
+ * Synchronises the stream at every Arnoldi step.
+ */
+typedef struct csl_helmholtz csl_helmholtz;
+typedef struct csl_helmholtz_info {
+  int iters;              /* Arnoldi steps (preconditioner applications)      */
+  int status;             /* CSL_OK when relres <= tol, else NOT_CONVERGED / error */
+  double relres;          /* true ||f - (K + lam_A I) u|| / ||f|| of the result */
+  int inner_iters_total;  /* MINRES iterations summed over the inner solves    */
+  int restarts;
+  int reserved[4];
+} csl_helmholtz_info;
+
+csl_status csl_helmholtz_create(csl_helmholtz** out, int dim, const int64_t n[3], const double* const coef_faces[3],
+                                double lam_re, double lam_im, double shift_re, double shift_im, int restart,
+                                const csl_plan_options* opt, void* stream);
+csl_status csl_helmholtz_solve(csl_helmholtz* h, const double* f, double* u, double tol, int maxit,
+                               double inner_tol, int inner_maxit, csl_helmholtz_info* info);
+void csl_helmholtz_destroy(csl_helmholtz* h);
+
 size_t csl_plan_workspace_bytes(const csl_plan* plan);
 
 /* Human-readable launch configuration the plan chose (autotuned or default). */

@@ -6,7 +6,7 @@ include/csl.h); this package is its ctypes binding plus a torch.autograd
 wrapper.  PyTorch supplies device memory and streams only.
 """
 from ._binding import (Batch, BREAKDOWN, CSLError, CUDA_ERROR, INVALID_ARG, Info, NOT_CONVERGED, OK,  # noqa: F401
-                       OUT_OF_MEMORY, PREC_BF16X3, PREC_BF16X6, PREC_FP32, PREC_FP64, ParaDiag, Plan,
+                       Helmholtz, OUT_OF_MEMORY, PREC_BF16X3, PREC_BF16X6, PREC_FP32, PREC_FP64, ParaDiag, Plan,
                        SINGULAR_PRECOND, TIMEOUT, UNSUPPORTED_SIZE, lib, precondition_static, status_string,
                        version)
 from .autograd import CSLSolve, solve  # noqa: F401

@@ -41,7 +41,18 @@ class ParaDiagInfo(ctypes.Structure):
                 ("inner_iters_max", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
+class HelmholtzInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double),
+                ("inner_iters_total", ctypes.c_int), ("restarts", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
 _SIGS = {
+    "csl_helmholtz_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(_P), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(PlanOptions), _P]),
+    "csl_helmholtz_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_int, ctypes.POINTER(HelmholtzInfo)]),
+    "csl_helmholtz_destroy": (None, [_P]),
     "csl_paradiag_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.POINTER(PlanOptions), _P]),
@@ -461,5 +472,59 @@ class ParaDiag:
                                     _dptr(g.contiguous(), ("complex128",), "g"), _dptr(u, ("complex128",), "u"),
                                     float(tol), int(maxit), float(inner_tol), int(inner_maxit), ctypes.byref(info))
         _check(st, "csl_paradiag_solve", allow=(OK, NOT_CONVERGED))
+        return u, info
+
+
+class Helmholtz:
+    """Flexible GMRES for (K + lam I) u = f (e.g. lam = -k^2) preconditioned by
+    the library's solve of (K + shift I) (csl_helmholtz_*)."""
+
+    def __init__(self, faces, lam: complex, shift: complex, restart: int = 30, precision: str = "fp64",
+                 autotune: bool = True, stream=None):
+        faces = [f.contiguous() for f in faces]
+        dim = len(faces)
+        nx = faces[0].shape[-1] - 1
+        ny = faces[0].shape[-2]
+        nz = faces[0].shape[-3] if dim == 3 else 1
+        self.shape = (ny, nx) if dim == 2 else (nz, ny, nx)
+        n = (ctypes.c_int64 * 3)(nx, ny, nz)
+        fp = (_P * 3)(*[_dptr(faces[d], ("float64",), "faces") if d < dim else None for d in range(3)])
+        opt = PlanOptions()
+        lib.csl_plan_options_init(ctypes.byref(opt))
+        opt.precision = _PREC[precision]
+        opt.autotune = 1 if autotune else 0
+        lam, shift = complex(lam), complex(shift)
+        h = _P()
+        _check(lib.csl_helmholtz_create(ctypes.byref(h), dim, n, fp, lam.real, lam.imag, shift.real, shift.imag,
+                                        int(restart), ctypes.byref(opt), _stream_handle(stream)),
+               "csl_helmholtz_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.csl_helmholtz_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, f, tol: float = 1e-8, maxit: int = 500, inner_tol: float = 1e-6, inner_maxit: int = 2000,
+              out=None):
+        torch = _torch()
+        u = torch.empty_like(f) if out is None else out
+        info = HelmholtzInfo()
+        st = lib.csl_helmholtz_solve(self._h, _dptr(f.contiguous(), ("complex128",), "f"),
+                                     _dptr(u, ("complex128",), "u"), float(tol), int(maxit), float(inner_tol),
+                                     int(inner_maxit), ctypes.byref(info))
+        _check(st, "csl_helmholtz_solve", allow=(OK, NOT_CONVERGED))
         return u, info
 
