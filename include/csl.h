@@ -21,7 +21,9 @@
  * Conventions shared by every entry point
  *  - Grids: dim = 2 or 3; n[0], n[1], n[2] are the interior point counts along
  *    x, y, z (n[2] ignored for dim = 2).  Every n[d] + 1 must be a power of two
- *    between 4 and 1024 (else CSL_UNSUPPORTED_SIZE).
+ *    between 4 and 1024; 2D grids may reach 8192 in FP64 and 4096 in the
+ *    FP32 / BF16 precisions, the sizes of the paper's larger tables (else
+ *    CSL_UNSUPPORTED_SIZE).
  *  - Grid vectors are C-order arrays with x fastest: point (ix, iy[, iz]) at
  *    index ix + n[0]*(iy + n[1]*iz).  "complex128" vectors hold interleaved
  *    (re, im) doubles; "block-pair" vectors hold (block-1, block-2) doubles of

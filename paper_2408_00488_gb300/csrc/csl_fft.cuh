@@ -433,7 +433,7 @@ template <typename T, int N>
 struct LineDst<T, N, 0> {
   typedef typename C2<T>::t c_t;
   enum { TPL = DstShape<N>::TPL, LS = dst_line_stride<N>(), BLOCK_SYNC = 0,
-         TP = DstShape<N>::R2 == 1 ? 0 : N };
+         TP = DstShape<N>::R2 == 1 ? 0 : N, GLOBAL_TABLES = 0 };
   static __device__ __forceinline__ int in_pos(int j) { return j; }
   static __device__ __forceinline__ int out_pos(int m) { return dst_out_pos<N>(m); }
   template <bool PERM_IN>
@@ -446,13 +446,147 @@ struct LineDst<T, N, 0> {
 template <typename T, int N, int V>
 struct LineDst {
   typedef typename C2<T>::t c_t;
-  enum { TPL = wide_tpl(V), LS = wide_line_stride<N, wide_tpl(V)>(), BLOCK_SYNC = 1, TP = wide_tp_size<N>() };
+  enum { TPL = wide_tpl(V), LS = wide_line_stride<N, wide_tpl(V)>(), BLOCK_SYNC = 1, TP = wide_tp_size<N>(),
+         GLOBAL_TABLES = 0 };
   static __device__ __forceinline__ int in_pos(int j) { return wpad(j); }
   static __device__ __forceinline__ int out_pos(int m) { return wide_out_pos<N, TPL>(m); }
   template <bool PERM_IN>
   static __device__ __forceinline__ void run(c_t* a, int t, const c_t* tw, const T* hs, const c_t* tp,
                                              c_t* scratch) {
     dst_line_wide<T, N, TPL, PERM_IN>(a, t, tw, hs, tp, scratch);
+  }
+  static __device__ __forceinline__ void line_sync() { __syncthreads(); }
+};
+
+// ---------------------------------------------------------------------------
+// Long lines (N = 2048 .. 8192, 2D grids of the paper's large tables): one
+// CTA of TPL lanes per line, an NP-pass Stockham autosort FFT (radices R0..R3)
+// whose inter-pass twiddles w_{Ls r}^{q k} = w_N^{q k N/(Ls r)} come from the
+// length-N table itself, so no per-pass tables exist; the line (up to 128 KB
+// in FP64) fills shared memory and the tables are read from global memory
+// through the cache.  Pre-twiddle, split and prefix scan as in the wide path.
+// ---------------------------------------------------------------------------
+template <int N> struct BigShape;
+template <> struct BigShape<2048> { enum { TPL = 256, NP = 3, R0 = 8, R1 = 16, R2 = 16, R3 = 1 }; };
+template <> struct BigShape<4096> { enum { TPL = 256, NP = 3, R0 = 16, R1 = 16, R2 = 16, R3 = 1 }; };
+template <> struct BigShape<8192> { enum { TPL = 512, NP = 4, R0 = 8, R1 = 8, R2 = 8, R3 = 16 }; };
+
+template <typename T, int N, int TPL, int R, int LSP, bool FIRST, bool PERM_IN>
+__device__ __forceinline__ void big_pass(typename C2<T>::t* a, int lane, const T* hs, const typename C2<T>::t* tw) {
+  typedef typename C2<T>::t c_t;
+  constexpr int G = N / R, PER = (G + TPL - 1) / TPL, H = N / 2;
+  constexpr bool FULL = (G % TPL) == 0;
+  constexpr int TSTEP = N / (LSP * R);  // w_{LSP R} = w_N^{TSTEP}
+  c_t x[PER][R];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int l = lane + TPL * i;
+    if (FULL || l < G) {
+      const int k = l & (LSP - 1);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int idx = l + q * G;
+        c_t v = FIRST ? wide_pre_twiddle<T, N, TPL, PERM_IN>(a, hs, idx) : a[wpad(idx)];
+        if (!FIRST && q > 0) v = cmul<T>(v, tw_full<T>(tw, (q * k * TSTEP) & (N - 1), H));
+        x[i][q] = v;
+      }
+      dft_reg<T, R, N / R>(x[i], tw);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int l = lane + TPL * i;
+    if (FULL || l < G) {
+      const int j = l / LSP, k = l & (LSP - 1);
+#pragma unroll
+      for (int s = 0; s < R; ++s) a[wpad(j * LSP * R + k + s * LSP)] = x[i][s];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, bool PERM_IN>
+__device__ __forceinline__ void dst_line_big(typename C2<T>::t* a, int t, const typename C2<T>::t* tw, const T* hs,
+                                             typename C2<T>::t* scratch) {
+  typedef typename C2<T>::t c_t;
+  typedef BigShape<N> S;
+  constexpr int TPL = S::TPL, R0 = S::R0, R1 = S::R1, R2 = S::R2, R3 = S::R3, H = N / 2, CH = H / TPL,
+                NW = TPL / 32, SBASE = H + TPL - 1;
+  big_pass<T, N, TPL, R0, 1, true, PERM_IN>(a, t, hs, tw);
+  big_pass<T, N, TPL, R1, R0, false, false>(a, t, hs, tw);
+  big_pass<T, N, TPL, R2, R0 * R1, false, false>(a, t, hs, tw);
+  if constexpr (S::NP == 4) big_pass<T, N, TPL, R3, R0 * R1 * R2, false, false>(a, t, hs, tw);
+  c_t cc[CH], ss[CH];
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const int k = t + TPL * i;
+    const c_t Yk = a[wpad(k)];
+    if (k == 0) {
+      cc[i] = Yk;
+      ss[i] = Yk;
+    } else {
+      const c_t Ym = a[wpad(N - k)];
+      cc[i] = cadd<T>(Yk, Ym);
+      ss[i] = mkc<T>(Ym.y - Yk.y, Yk.x - Ym.x);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const int k = t + TPL * i;
+    a[wpad(k + k / CH)] = cc[i];
+    if (k != 0) a[wpad(SBASE + k - 1)] = ss[i];
+  }
+  __syncthreads();
+  // prefix sum of C in FP64 whatever T is (the odd outputs are partial sums
+  // of up to N/2 terms); the inputs and outputs stay in T
+  double2 v[CH];
+  double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    v[i] = to_d2(a[wpad(t * (CH + 1) + i)]);
+    sum.x += v[i].x;
+    sum.y += v[i].y;
+  }
+  double2 inc = sum;
+  const int lw = t & 31, w = t >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double ux = __shfl_up_sync(0xffffffffu, inc.x, d);
+    const double uy = __shfl_up_sync(0xffffffffu, inc.y, d);
+    if (lw >= d) {
+      inc.x += ux;
+      inc.y += uy;
+    }
+  }
+  double2* dscr = reinterpret_cast<double2*>(scratch);
+  if (lw == 31) dscr[w] = inc;
+  __syncthreads();
+  for (int u = 0; u < w; ++u) {
+    inc.x += dscr[u].x;
+    inc.y += dscr[u].y;
+  }
+  double2 run = make_double2(inc.x - sum.x, inc.y - sum.y);
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    run.x += v[i].x;
+    run.y += v[i].y;
+    a[wpad(t * (CH + 1) + i)] = from_d2<T>(run);
+  }
+  __syncthreads();
+}
+
+template <typename T, int N>
+struct LineDst<T, N, 3> {
+  typedef typename C2<T>::t c_t;
+  enum { TPL = BigShape<N>::TPL, LS = wide_line_stride<N, BigShape<N>::TPL>(), BLOCK_SYNC = 1, TP = 0,
+         GLOBAL_TABLES = 1 };
+  static __device__ __forceinline__ int in_pos(int j) { return wpad(j); }
+  static __device__ __forceinline__ int out_pos(int m) { return wide_out_pos<N, TPL>(m); }
+  template <bool PERM_IN>
+  static __device__ __forceinline__ void run(c_t* a, int t, const c_t* tw, const T* hs, const c_t*, c_t* scratch) {
+    dst_line_big<T, N, PERM_IN>(a, t, tw, hs, scratch);
   }
   static __device__ __forceinline__ void line_sync() { __syncthreads(); }
 };

@@ -29,6 +29,7 @@ cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLau
 template <typename T>
 cudaError_t launch_row(int N, int wide, int load, int store, const RowArgs<T>& a, const PassLaunch& L,
                        cudaStream_t s, const RowArgs<T>* batch, int nsys) {
+  if (pass_is_big(N)) return launch_row_big<T>(N, load, store, a, L, s, batch, nsys);
   switch (N) {
 #define CASE(NN)                                                                    \
   case NN:                                                                          \
@@ -60,6 +61,7 @@ cudaError_t launch_strided(int N, int wide, bool mid, const StridedArgs<T>& a, c
   if constexpr (sizeof(T) == 4) {
     if (L.tc) return launch_strided_tc(N, L.tc, mid, a, L, s, batch, nsys);
   }
+  if (pass_is_big(N)) return launch_strided_big<T>(N, mid, a, L, s, batch, nsys);
   switch (N) {
 #define CASE(NN)                                                                  \
   case NN:                                                                        \
@@ -72,18 +74,6 @@ cudaError_t launch_strided(int N, int wide, bool mid, const StridedArgs<T>& a, c
 #undef CASE
   }
   return cudaErrorInvalidValue;
-}
-
-// dynamic shared memory limit of one kernel = opt-in maximum - its static shared memory
-inline cudaError_t allow_dyn_smem(const void* k) {
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  return e;
 }
 
 template <typename T>
@@ -108,6 +98,7 @@ cudaError_t set_pass_attrs() {
   VARIANT(1024, 2)
 #undef VARIANT
 #undef SETA
+  if (e == cudaSuccess) e = set_pass_attrs_big<T>();
   return e;
 }
 

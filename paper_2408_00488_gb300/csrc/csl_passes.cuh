@@ -20,7 +20,7 @@
 
 // FP32 passes: two CTAs of 256 threads per SM (at most 128 registers per
 // thread); the FP64 lines need the full register file
-#define CSL_PASS_MINB(T, V) (sizeof(T) == 4 ? ((V) == 2 ? 3 : 2) : 1)
+#define CSL_PASS_MINB(T, V) (sizeof(T) == 4 && (V) < 3 ? ((V) == 2 ? 3 : 2) : 1)
 
 namespace csl {
 
@@ -69,22 +69,36 @@ struct StridedArgs {
 
 // byte offsets of the shared-memory regions: twiddles | half sines | extra
 // twiddles | scan scratch (2 per line) | lines
+// (long lines, variant 3, read their tables from global memory)
 template <typename T, int N, int WIDE>
 __host__ __device__ constexpr size_t pass_tables_bytes() {
-  return (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16 +
-         (size_t)line_tp_size(N, WIDE) * sizeof(typename C2<T>::t);
+  return LineDst<T, N, WIDE>::GLOBAL_TABLES
+             ? 0
+             : (size_t)(N / 2) * sizeof(typename C2<T>::t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16 +
+                   (size_t)line_tp_size(N, WIDE) * sizeof(typename C2<T>::t);
+}
+// scan scratch per line: one complex per warp of the line (at least 4; the
+// long-line variant scans in FP64, so twice as many T-complex slots)
+template <typename T, int N, int WIDE>
+__host__ __device__ constexpr int pass_scratch() {
+  return (LineDst<T, N, WIDE>::TPL / 32 > 4 ? LineDst<T, N, WIDE>::TPL / 32 : 4) * (WIDE == 3 ? 2 : 1);
 }
 template <typename T, int N, int WIDE>
 __host__ __device__ constexpr size_t pass_smem_bytes(int lines) {
-  return pass_tables_bytes<T, N, WIDE>() + (size_t)lines * 4 * sizeof(typename C2<T>::t) +
+  return pass_tables_bytes<T, N, WIDE>() + (size_t)lines * pass_scratch<T, N, WIDE>() * sizeof(typename C2<T>::t) +
          (size_t)lines * LineDst<T, N, WIDE>::LS * sizeof(typename C2<T>::t);
+}
+// CTA size bound of the pass kernels: 256, or one long line's lanes
+template <int N, int WIDE>
+__host__ __device__ constexpr int pass_max_threads() {
+  return WIDE == 3 ? (N >= 8192 ? 512 : 256) : 256;
 }
 
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
 template <typename T, int N, int WIDE, int LOAD, int STORE>
-__global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
+__global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -99,13 +113,21 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> 
   constexpr int UB = NL < UBMAX ? NL : UBMAX;
   if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c_t* s_tw = (c_t*)smem_raw;
-  T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
-  c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  c_t* w_tw = (c_t*)smem_raw;
+  T* w_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
+  c_t* w_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  const c_t* s_tw = w_tw;
+  const T* s_hs = w_hs;
+  const c_t* s_tp = w_tp;
   const int nlines = blockDim.x / TPL;
   c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
-  c_t* lines = s_scr + 4 * nlines;
-  load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
+  c_t* lines = s_scr + pass_scratch<T, N, WIDE>() * nlines;
+  if constexpr (D::GLOBAL_TABLES) {
+    s_tw = a.tw;
+    s_hs = a.hs;
+  } else {
+    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);
+  }
   double lz = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
   if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
   // MINRES works with the normalised z_{j+1} / gamma_{j+1}; gamma_{j+1} is
@@ -251,7 +273,7 @@ __device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, 
 }
 
 template <typename T, int N, int WIDE, bool MID>
-__global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
+__global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, WIDE)) k_strided(StridedArgs<T> a0, const StridedArgs<T>* batch, int bps) {
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -263,13 +285,21 @@ __global__ void __launch_bounds__(256, CSL_PASS_MINB(T, WIDE)) k_strided(Strided
   constexpr int UB = NL < 8 ? NL : 8;
   if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c_t* s_tw = (c_t*)smem_raw;
-  T* s_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
-  c_t* s_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  c_t* w_tw = (c_t*)smem_raw;
+  T* w_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
+  c_t* w_tp = (c_t*)(smem_raw + (size_t)(N / 2) * sizeof(c_t) + (((size_t)(N / 2 + 1) * sizeof(T) + 15) / 16) * 16);
+  const c_t* s_tw = w_tw;
+  const T* s_hs = w_hs;
+  const c_t* s_tp = w_tp;
   const int C = blockDim.x / TPL;  // lines (columns) per tile, a power of two
   c_t* s_scr = (c_t*)(smem_raw + pass_tables_bytes<T, N, WIDE>());
-  c_t* lines = s_scr + 4 * C;
-  load_tables<T>(s_tw, s_hs, s_tp, a.tw, a.hs, a.tp, N, D::TP);
+  c_t* lines = s_scr + pass_scratch<T, N, WIDE>() * C;
+  if constexpr (D::GLOBAL_TABLES) {
+    s_tw = a.tw;
+    s_hs = a.hs;
+  } else {
+    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);
+  }
   int logC = 0;
   while ((1 << logC) < C) ++logC;
   const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
@@ -355,9 +385,18 @@ struct PassLaunch {
 inline bool pass_has_wide(int N) { return N == 512 || N == 1024; }
 inline int pass_num_variants(int N) { return pass_has_wide(N) ? 3 : 1; }
 
+// Long lines (N = 2048 .. 8192): variant 3 only, one line per CTA; their
+// instantiations live in csl_pass32_big.cu / csl_pass64_big.cu.
+#define CSL_FOR_EACH_BIG_N(X) X(2048) X(4096) X(8192)
+inline bool pass_is_big(int N) { return N > 1024; }
+
 template <typename T>
 size_t pass_smem(int N, int wide, int lines) {
   switch (N) {
+#define BIGCASE(NN) \
+  case NN: return pass_smem_bytes<T, NN, 3>(lines);
+    CSL_FOR_EACH_BIG_N(BIGCASE)
+#undef BIGCASE
 #define CASE(NN)                                                                       \
   case NN:                                                                             \
     if constexpr (NN >= 512) {                                                         \
@@ -382,6 +421,10 @@ inline int pass_tpl_n(int wide) {
 
 inline int pass_tpl(int N, int wide) {
   switch (N) {
+#define BIGCASE(NN) \
+  case NN: return LineDst<float, NN, 3>::TPL;
+    CSL_FOR_EACH_BIG_N(BIGCASE)
+#undef BIGCASE
 #define CASE(NN) \
   case NN: return pass_tpl_n<NN>(wide);
     CSL_FOR_EACH_N(CASE)
@@ -398,8 +441,28 @@ cudaError_t launch_row(int N, int wide, int load, int store, const RowArgs<T>& a
 template <typename T>
 cudaError_t launch_strided(int N, int wide, bool mid, const StridedArgs<T>& a, const PassLaunch& L,
                            cudaStream_t s, const StridedArgs<T>* batch = nullptr, int nsys = 0);
+// dynamic shared memory limit of one kernel = opt-in maximum - its static shared memory
+inline cudaError_t allow_dyn_smem(const void* k) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 template <typename T>
 cudaError_t set_pass_attrs();
+template <typename T>
+cudaError_t launch_row_big(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s,
+                           const RowArgs<T>* batch, int nsys);
+template <typename T>
+cudaError_t launch_strided_big(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s,
+                               const StridedArgs<T>* batch, int nsys);
+template <typename T>
+cudaError_t set_pass_attrs_big();
 
 // tensor-core strided passes (csl_tc.cu): lines of N = 32, 64 or 128 points
 bool tc_supported(int N);
