@@ -331,6 +331,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched config-3 line")
     ap.add_argument("--no-config2", action="store_true", help="skip the config-2 forms (FFT vs tensor-core DST)")
     ap.add_argument("--no-paradiag", action="store_true", help="skip the all-at-once time-solve line")
+    ap.add_argument("--no-tables", action="store_true", help="skip the paper's table rows at n = 1023 and 4095")
     ap.add_argument("--profile", choices=["config1", "config2"], default=None,
                     help="solve once, then launch each kernel of one MINRES iteration inside an "
                          "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32 "
@@ -545,6 +546,36 @@ def main():
                   "sequential_estimate_ms": L3 * ms_step, "step_iters": sinfo.iters,
                   "speedup_vs_sequential": L3 * ms_step / ms_pd}
 
+    # ---- the paper's Tables 1(a) / 2(a) rows (FP64 form, as the paper) -----
+    # CPU seconds the paper prints (Table 1(a): a = 1; Table 2(a): a =
+    # (20+x^2)(20+y^2); Octave on 2x Xeon Gold 6246R), context only
+    paper_s = {("1a", 1023): [0.89, 0.82, 0.83, 0.83, 0.99, 0.93],
+               ("1a", 4095): [20.65, 22.71, 20.71, 20.55, 23.22, 23.09],
+               ("2a", 1023): [4.59, 4.67, 4.14, 4.47, 4.13, 4.34],
+               ("2a", 4095): [114.74, 114.66, 110.62, 109.70, 111.25, 110.60]}
+    tables = None
+    if not args.no_tables:
+        tables = {"workload": "Tables 1(a)/2(a) rows: 2D n in {1023, 4095}, a = 1 (1a) or (20+x^2)(20+y^2) (2a), "
+                              "the paper's six (alpha, beta) per table, f ~ N(0,1)^2 seed 81, tol 1e-8, FP64 form; "
+                              "ms = one solve (plan set-up excluded, as the paper's timings are per solve)",
+                  "rows": []}
+        for (tab, nt), cpu_s in paper_s.items():
+            coef = W.coef_const(1.0) if tab == "1a" else W.coef_table2
+            shifts = W.TABLE1_SHIFTS if tab == "1a" else W.TABLE2_SHIFTS
+            ft = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in W.sample_faces(2, nt, coef)]
+            fr = torch.from_numpy(W.rhs_normal((nt, nt), 81)).to(dev)
+            zt = torch.empty_like(fr)
+            for (al, be), cs in zip(shifts, cpu_s):
+                with csl.Plan(ft, al + 1j * be, precision="fp64") as pt:
+                    pt.solve(fr, tol=TOL, maxit=MAXIT, out=zt)
+                    ms_t, it_t = timed(lambda: pt.solve(fr, tol=TOL, maxit=MAXIT, out=zt)[1], 3,
+                                       f"timed_table_{tab}_{nt}")
+                assert it_t.converged
+                tables["rows"].append({"table": tab, "n": nt, "alpha": al, "beta": be, "iters": it_t.iters,
+                                       "ms": round(ms_t, 3), "paper_iters": 2 if tab == "1a" else 14,
+                                       "paper_cpu_s": cs, "ratio_vs_paper_cpu": round(cs * 1e3 / ms_t, 1)})
+            del ft, fr, zt
+
     # ---- CPU baseline: the oracle on a bounded sample ----------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -571,6 +602,7 @@ def main():
             "batched": batched,
             "config2_forms": cfg2,
             "paradiag": pdline,
+            "paper_tables": tables,
             "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
