@@ -192,6 +192,14 @@ void config_row(PassCfg& c, int n, int nrows) {
   c.N = n + 1;
   c.nouter = nrows;
   c.ncols = n;
+  if (c.N == 16384) {  // FP64: one two-CTA cluster per row
+    c.wide = 4;
+    c.lines = 1;
+    c.L.threads = cluster_pass_threads();
+    c.L.smem = cluster_pass_smem();
+    c.L.blocks = 2 * (nrows < 456 ? nrows : 456);
+    return;
+  }
   if (pass_is_big(c.N)) {  // one CTA of all the line's lanes per row
     c.wide = 3;
     c.lines = 1;
@@ -217,6 +225,15 @@ void config_strided(PassCfg& c, int n, int ncols, int nouter, long outer_stride,
   c.nouter = nouter;
   c.outer_stride = outer_stride;
   c.line_stride = line_stride;
+  if (c.N == 16384) {  // FP64: one two-CTA cluster per column
+    c.wide = 4;
+    c.lines = 1;
+    c.L.threads = cluster_pass_threads();
+    c.L.smem = cluster_pass_smem();
+    const long cols = (long)ncols * nouter;
+    c.L.blocks = (int)(2 * (cols < kMaxRedBlocks / 2 ? cols : kMaxRedBlocks / 2));
+    return;
+  }
   if (pass_is_big(c.N)) {  // one column per CTA
     c.wide = 3;
     c.lines = 1;
@@ -482,7 +499,7 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
 template <typename T>
 cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e0, cudaEvent_t e1,
                       const DevState& hst) {
-  if (c.L.tc || c.wide == 3) return cudaSuccess;  // the tensor-core and long-line variants have one shape
+  if (c.L.tc || c.wide >= 3) return cudaSuccess;  // the tensor-core and long-line variants have one shape
   const TuneKey key = {(int)sizeof(T), kind, c.N, c.ncols, c.nouter};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -710,10 +727,10 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   csl_plan_options o;
   csl_plan_options_init(&o);
   if (opt) o = *opt;
-  // transform lengths: 4 .. 1024 in 2D and 3D; 2D grids up to 8192 in FP64
-  // (a longer FP64 line would not fit in shared memory) and 4096 in the FP32
-  // forms, whose P^{-1} error grows like eps_32 kappa(P), kappa(P) ~ n^2
-  const long nmax = dim == 3 ? 1024 : (o.precision == CSL_PREC_FP64 ? 8192 : 4096);
+  // transform lengths: 4 .. 1024 in 2D and 3D; 2D grids up to 16384 in FP64
+  // (lines of 16384 on two-CTA clusters) and 4096 in the FP32 forms, whose
+  // P^{-1} error grows like eps_32 kappa(P), kappa(P) ~ n^2
+  const long nmax = dim == 3 ? 1024 : (o.precision == CSL_PREC_FP64 ? 16384 : 4096);
   for (int d = 0; d < dim; ++d) {
     if (!coef_faces[d] || n[d] < 1) return CSL_INVALID_ARG;
     if (n[d] + 1 < 4 || n[d] + 1 > nmax || ilog2_exact(n[d] + 1) < 0) return CSL_UNSUPPORTED_SIZE;
@@ -992,6 +1009,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
                       nm[d], cs[d]->N,
                       cs[d]->L.tc == 2   ? "tcgen05-bf16x3"
                       : cs[d]->L.tc == 3 ? "tcgen05-bf16x6"
+                      : cs[d]->wide == 4 ? "cluster2"
                       : cs[d]->wide == 3 ? "long-line"
                       : cs[d]->wide == 2 ? "stockham128"
                       : cs[d]->wide == 1 ? "stockham64"

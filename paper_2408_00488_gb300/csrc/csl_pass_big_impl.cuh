@@ -30,6 +30,12 @@ cudaError_t launch_row_big_n(int load, int store, const RowArgs<T>& a, const Pas
 template <typename T>
 cudaError_t launch_row_big(int N, int load, int store, const RowArgs<T>& a, const PassLaunch& L, cudaStream_t s,
                            const RowArgs<T>* batch, int nsys) {
+  if (N == 16384) {  // FP64 only, single systems: two-CTA cluster per line
+    if constexpr (sizeof(T) == 8) {
+      if (!batch) return launch_row_cl(load, store, a, L, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (N) {
 #define CASE(NN) \
   case NN: return launch_row_big_n<T, NN>(load, store, a, L, s, batch, nsys);
@@ -42,6 +48,12 @@ cudaError_t launch_row_big(int N, int load, int store, const RowArgs<T>& a, cons
 template <typename T>
 cudaError_t launch_strided_big(int N, bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s,
                                const StridedArgs<T>* batch, int nsys) {
+  if (N == 16384) {
+    if constexpr (sizeof(T) == 8) {
+      if (!batch) return launch_strided_cl(mid, a, L, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   const int grid = batch ? L.blocks * nsys : L.blocks;
   switch (N) {
 #define CASE(NN)                                                                              \
@@ -73,6 +85,9 @@ cudaError_t set_pass_attrs_big() {
   CSL_FOR_EACH_BIG_N(CASE)
 #undef CASE
 #undef SETA
+  if constexpr (sizeof(T) == 8) {
+    if (e == cudaSuccess) e = set_cluster_attrs();
+  }
   return e;
 }
 

@@ -463,6 +463,12 @@ cudaError_t launch_strided_big(int N, bool mid, const StridedArgs<T>& a, const P
                                const StridedArgs<T>* batch, int nsys);
 template <typename T>
 cudaError_t set_pass_attrs_big();
+// FP64 lines of 16384 points on a two-CTA cluster (csl_cluster.cu)
+size_t cluster_pass_smem();
+int cluster_pass_threads();
+cudaError_t launch_row_cl(int load, int store, const RowArgs<double>& a, const PassLaunch& L, cudaStream_t s);
+cudaError_t launch_strided_cl(bool mid, const StridedArgs<double>& a, const PassLaunch& L, cudaStream_t s);
+cudaError_t set_cluster_attrs();
 
 // tensor-core strided passes (csl_tc.cu): lines of N = 32, 64 or 128 points
 bool tc_supported(int N);

@@ -71,8 +71,7 @@ def test_host_side_argument_validation(csl):
     assert _create(csl, 2, (7, 7, 1), (fake, None, None))[0] == b.INVALID_ARG
     assert _create(csl, 2, (0, 7, 1), (fake, fake, None))[0] == b.INVALID_ARG
     assert _create(csl, 2, (8, 7, 1), (fake, fake, None))[0] == b.UNSUPPORTED_SIZE
-    # 2D lines up to 8192 points in FP64 (4096 in the FP32 forms), 3D up to 1024
-    assert _create(csl, 2, (16383, 7, 1), (fake, fake, None))[0] == b.UNSUPPORTED_SIZE
+    # 2D lines up to 16384 points in FP64 (4096 in the FP32 forms), 3D up to 1024
     assert _create(csl, 2, (32767, 7, 1), (fake, fake, None))[0] == b.UNSUPPORTED_SIZE
     assert _create(csl, 3, (2047, 7, 7), (fake, fake, fake))[0] == b.UNSUPPORTED_SIZE
     assert _create(csl, 3, (7, 7, 2), (fake, fake, fake))[0] == b.UNSUPPORTED_SIZE
