@@ -84,7 +84,10 @@ typedef struct csl_plan_options {
   int autotune;           /* 1 (default): time the candidate CTA shapes and transform
                              variants of each pass at plan creation and keep the fastest
                              (cached per shape for the process); 0: built-in defaults      */
-  int reserved[7];
+  int programmatic_launch; /* 1 (default): the iteration's kernels are launched with
+                             programmatic dependent launch, so each may start (tables,
+                             set-up) while its predecessor drains; 0: plain launches       */
+  int reserved[6];
 } csl_plan_options;
 
 typedef struct csl_solve_info {

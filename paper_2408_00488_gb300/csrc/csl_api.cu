@@ -108,6 +108,7 @@ struct csl_plan {
   double alpha = 0, beta = 0, gamma = 0, amin = 0, amax = 0, sqrt_pmin = 0, sqrt_pmax = 0;
   int precision = CSL_PREC_FP64;
   int use_graph = 1;
+  int use_pdl = 1;  // programmatic dependent launch of the iteration's kernels
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   std::vector<void*> allocs;
@@ -357,11 +358,9 @@ cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) 
   a.cond = P->cond;
   a.use_cond = use_cond ? 1 : 0;
   typedef typename C2<T>::t TZ;
-  if (P->dim == 2)
-    k_stencil<2, TZ><<<P->sten_blocks, 256, 0, s>>>(a, nullptr, 0);
-  else
-    k_stencil<3, TZ><<<P->sten_blocks, 256, 0, s>>>(a, nullptr, 0);
-  return cudaGetLastError();
+  const StencilArgs* nob = nullptr;
+  if (P->dim == 2) return launch_k(P->use_pdl != 0, k_stencil<2, TZ>, P->sten_blocks, 256, 0, s, a, nob, 0);
+  return launch_k(P->use_pdl != 0, k_stencil<3, TZ>, P->sten_blocks, 256, 0, s, a, nob, 0);
 }
 
 template <typename T>
@@ -715,6 +714,7 @@ csl_status csl_plan_options_init(csl_plan_options* opt) {
   opt->lines_per_cta = 0;
   opt->use_graph = 1;
   opt->autotune = 1;
+  opt->programmatic_launch = 1;
   return CSL_OK;
 }
 
@@ -745,6 +745,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   P->dim = dim;
   P->precision = o.precision;
   P->use_graph = o.use_graph;
+  P->use_pdl = o.programmatic_launch;
   P->stream = (cudaStream_t)stream;
   P->alpha = alpha;
   P->beta = beta;
@@ -984,6 +985,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       return CSL_CUDA_ERROR;
     }
   }
+  P->row.L.pdl = P->sy.L.pdl = P->sz.L.pdl = P->use_pdl;
   if (o.autotune && o.lines_per_cta <= 0) {
     // (the chosen shapes are described in P->config below)
     err = o.precision != CSL_PREC_FP64 ? autotune<float>(P) : autotune<double>(P);
@@ -1423,11 +1425,10 @@ cudaError_t group_iteration(csl_batch* B, BatchGroup& G, int par, cudaStream_t s
   typedef typename C2<T>::t TZ;
   StencilArgs sd;
   memset(&sd, 0, sizeof(sd));
-  if (P->dim == 2)
-    k_stencil<2, TZ><<<P->sten_blocks * ns, 256, 0, s>>>(sd, G.d_sten[par], P->sten_blocks);
-  else
-    k_stencil<3, TZ><<<P->sten_blocks * ns, 256, 0, s>>>(sd, G.d_sten[par], P->sten_blocks);
-  cudaError_t e = cudaGetLastError();
+  const StencilArgs* sb = (const StencilArgs*)G.d_sten[par];
+  cudaError_t e =
+      P->dim == 2 ? launch_k(P->use_pdl != 0, k_stencil<2, TZ>, P->sten_blocks * ns, 256, 0, s, sd, sb, P->sten_blocks)
+                  : launch_k(P->use_pdl != 0, k_stencil<3, TZ>, P->sten_blocks * ns, 256, 0, s, sd, sb, P->sten_blocks);
   RowArgs<T> rd;
   memset(&rd, 0, sizeof(rd));
   if (e == cudaSuccess)

@@ -100,6 +100,15 @@ enum {
   ST_NOT_CONVERGED = 5, ST_TIMEOUT = 6, ST_CUDA = 7, ST_OOM = 8
 };
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor in the
+// stream is still running: pdl_wait() blocks until the predecessor grid has
+// completed and its memory is visible (a no-op after a normal launch), so it
+// precedes every read of data an earlier kernel wrote; pdl_trigger() lets
+// the next grid launch once every CTA of this grid has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -168,6 +177,24 @@ __device__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned 
 #pragma unroll
   for (int i = 0; i < NV; ++i) tot[i] = s_tot[i];
   return true;
+}
+
+// Launch k<<<grid, block, smem, s>>>(args...), with the programmatic
+// stream-serialisation attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
 }  // namespace csl

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
   const int nblk = batch ? bps : (int)gridDim.x;
   const StencilArgs a = batch ? batch[sys] : a0;
   DevState* st = a.st;
+  pdl_wait();
   if (st->done) {
     // keep the device-side loop closed whatever set `done` (Givens breakdown, cap, ...)
     if (a.use_cond && bid == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
@@ -344,6 +345,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
       if (check) wx.advance();
     }
   }
+  pdl_trigger();
   double tot[2];
   if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;

@@ -12,18 +12,16 @@ cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLau
   const int grid = batch ? L.blocks * nsys : L.blocks;
   const int bps = L.blocks;
   if (load == LOAD_V && store == STORE_T)
-    k_row<T, N, W, LOAD_V, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+    return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_V, STORE_T>, grid, L.threads, L.smem, s, a, batch, bps);
   else if (load == LOAD_LANCZOS && store == STORE_T)
-    k_row<T, N, W, LOAD_LANCZOS, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+    return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_LANCZOS, STORE_T>, grid, L.threads, L.smem, s, a, batch, bps);
   else if (load == LOAD_T && store == STORE_Z)
-    k_row<T, N, W, LOAD_T, STORE_Z><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+    return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_T, STORE_Z>, grid, L.threads, L.smem, s, a, batch, bps);
   else if (load == LOAD_T && store == STORE_Z_UPDATE)
-    k_row<T, N, W, LOAD_T, STORE_Z_UPDATE><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+    return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_T, STORE_Z_UPDATE>, grid, L.threads, L.smem, s, a, batch, bps);
   else if (load == LOAD_T && store == STORE_D)
-    k_row<T, N, W, LOAD_T, STORE_D><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+    return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_T, STORE_D>, grid, L.threads, L.smem, s, a, batch, bps);
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -48,11 +46,8 @@ template <typename T, int N, int W>
 cudaError_t launch_strided_n(bool mid, const StridedArgs<T>& a, const PassLaunch& L, cudaStream_t s,
                              const StridedArgs<T>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
-  if (mid)
-    k_strided<T, N, W, true><<<grid, L.threads, L.smem, s>>>(a, batch, L.blocks);
-  else
-    k_strided<T, N, W, false><<<grid, L.threads, L.smem, s>>>(a, batch, L.blocks);
-  return cudaGetLastError();
+  if (mid) return launch_k(L.pdl != 0, k_strided<T, N, W, true>, grid, L.threads, L.smem, s, a, batch, L.blocks);
+  return launch_k(L.pdl != 0, k_strided<T, N, W, false>, grid, L.threads, L.smem, s, a, batch, L.blocks);
 }
 
 template <typename T>

@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   // element in flight, so they batch fewer elements (128-register FP32 budget)
   constexpr int UBMAX = STORE == STORE_Z_UPDATE ? 2 : LOAD == LOAD_LANCZOS ? 4 : 8;
   constexpr int UB = NL < UBMAX ? NL : UBMAX;
-  if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* w_tw = (c_t*)smem_raw;
   T* w_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
@@ -126,8 +125,10 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     s_tw = a.tw;
     s_hs = a.hs;
   } else {
-    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);
+    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);  // constant: may overlap the predecessor
   }
+  pdl_wait();
+  if (a.st && a.st->done) return;
   double lz = 0.0, wb = 0.0, wc = 0.0, xc = 0.0;
   if (LOAD == LOAD_LANCZOS) lz = a.st->delta / a.st->gam;
   // MINRES works with the normalised z_{j+1} / gamma_{j+1}; gamma_{j+1} is
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     }
     D::line_sync();
   }
+  pdl_trigger();
 }
 
 // End of a MID pass: grid sum of the Parseval partials; the last CTA either
@@ -283,7 +285,6 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;
   constexpr int UB = NL < 8 ? NL : 8;
-  if (a.st && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* w_tw = (c_t*)smem_raw;
   T* w_hs = (T*)(smem_raw + (size_t)(N / 2) * sizeof(c_t));
@@ -298,8 +299,10 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     s_tw = a.tw;
     s_hs = a.hs;
   } else {
-    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);
+    load_tables<T>(w_tw, w_hs, w_tp, a.tw, a.hs, a.tp, N, D::TP);  // constant: may overlap the predecessor
   }
+  pdl_wait();
+  if (a.st && a.st->done) return;
   int logC = 0;
   while ((1 << logC) < C) ++logC;
   const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
       if (c < Ch) a.data[base + (long)j * a.line_stride + c] = lines[(size_t)c * LS + D::out_pos(j + 1)];
     }
   }
+  pdl_trigger();
   if (MID && a.scalar_mode != 0) mid_scalar_tail<T>(a, g2acc, bid, nblk);
 }
 
@@ -375,7 +379,8 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
 struct PassLaunch {
   int blocks, threads;
   size_t smem;
-  int tc = 0;  // strided passes: 0 = FFT, 2 or 3 = tensor-core GEMM with that many bf16 terms
+  int tc = 0;   // strided passes: 0 = FFT, 2 or 3 = tensor-core GEMM with that many bf16 terms
+  int pdl = 0;  // launch with programmatic dependent launch (overlaps the predecessor's tail)
 };
 
 #define CSL_FOR_EACH_N(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)

@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
   const int nblk = batch ? bps : (int)gridDim.x;
   const StridedArgs<float> a = batch ? batch[sys] : a0;
+  pdl_wait();
   if (a.st && a.st->done) return;
 
   extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_before();
     __syncthreads();  // operands and TMEM free for the next tile
   }
+  pdl_trigger();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
@@ -392,8 +394,7 @@ template <int N, bool MID, int SPLIT>
 cudaError_t launch_tc_n(const StridedArgs<float>& a, const PassLaunch& L, cudaStream_t s,
                         const StridedArgs<float>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
-  k_strided_tc<N, MID, SPLIT><<<grid, kTcThreads, L.smem, s>>>(a, batch, L.blocks);
-  return cudaGetLastError();
+  return launch_k(L.pdl != 0, k_strided_tc<N, MID, SPLIT>, grid, kTcThreads, L.smem, s, a, batch, L.blocks);
 }
 
 template <int N, bool MID, int SPLIT>
