@@ -21,7 +21,7 @@
  * Conventions shared by every entry point
  *  - Grids: dim = 2 or 3; n[0], n[1], n[2] are the interior point counts along
  *    x, y, z (n[2] ignored for dim = 2).  Every n[d] + 1 must be a power of two
- *    between 4 and 1024; 2D grids may reach 8192 in FP64 and 4096 in the
+ *    between 4 and 1024; 2D grids may reach 16384 in FP64 and 4096 in the
  *    FP32 / BF16 precisions, the sizes of the paper's larger tables (else
  *    CSL_UNSUPPORTED_SIZE).
  *  - Grid vectors are C-order arrays with x fastest: point (ix, iy[, iz]) at
@@ -52,8 +52,9 @@ extern "C" {
 
 typedef enum csl_status {
   CSL_OK = 0,
-  CSL_INVALID_ARG = 1,       /* null pointer, dim not 2/3, n < 1, non-finite shift, coefficient <= 0 */
-  CSL_UNSUPPORTED_SIZE = 2,  /* n[d] + 1 not a power of two in [4, 1024] */
+  CSL_INVALID_ARG = 1,       /* null pointer, dim not 2/3, n < 1, non-finite shift, coefficient <= 0;
+                                FP32 / BF16 forms: per-mode scales of P^-1 outside the FP32 range */
+  CSL_UNSUPPORTED_SIZE = 2,  /* n[d] + 1 not a power of two in the ranges above */
   CSL_SINGULAR_PRECOND = 3,  /* some (gamma mu_k + alpha)^2 + beta^2 == 0 (only possible when beta == 0) */
   CSL_BREAKDOWN = 4,         /* non-finite or negative <P^{-1} v, v> in the Lanczos process */
   CSL_NOT_CONVERGED = 5,     /* maxit reached; z holds the last iterate, info is filled */
@@ -87,7 +88,11 @@ typedef struct csl_plan_options {
   int programmatic_launch; /* 1 (default): the iteration's kernels are launched with
                              programmatic dependent launch, so each may start (tables,
                              set-up) while its predecessor drains; 0: plain launches       */
-  int reserved[6];
+  int float_pair_stencil;  /* FP32 / BF16X3 / BF16X6 only. 1 (default): the stencil forms
+                             (K + alpha I) z in float-pair arithmetic in difference form
+                             (used while every face a/h^2, alpha and beta lie in
+                             [2^-60, 2^60]); 0: FP64 arithmetic, direct form               */
+  int reserved[5];
 } csl_plan_options;
 
 typedef struct csl_solve_info {

@@ -20,7 +20,8 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32, "bf16x3": PRE
 class PlanOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gamma_override", ctypes.c_double),
                 ("lines_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("programmatic_launch", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("autotune", ctypes.c_int), ("programmatic_launch", ctypes.c_int),
+                ("float_pair_stencil", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -181,7 +182,8 @@ class Plan:
 
     def __init__(self, faces: Sequence, lam: complex, precision: str = "fp64",
                  gamma: Optional[float] = None, lines_per_cta: int = 0, use_graph: bool = True,
-                 autotune: bool = True, stream=None, programmatic_launch: bool = True):
+                 autotune: bool = True, stream=None, programmatic_launch: bool = True,
+                 float_pair_stencil: bool = True):
         torch = _torch()
         dim = len(faces)
         if dim not in (2, 3):
@@ -207,6 +209,7 @@ class Plan:
         opt.use_graph = 1 if use_graph else 0
         opt.autotune = 1 if autotune else 0
         opt.programmatic_launch = 1 if programmatic_launch else 0
+        opt.float_pair_stencil = 1 if float_pair_stencil else 0
         self.precision = precision
         h = _P()
         st = lib.csl_plan_create(ctypes.byref(h), dim, n, ptrs, self.lam.real, self.lam.imag,

@@ -106,14 +106,18 @@ struct csl_plan {
   long M = 0;
   double h[3] = {1, 1, 1};
   double alpha = 0, beta = 0, gamma = 0, amin = 0, amax = 0, sqrt_pmin = 0, sqrt_pmax = 0;
+  double sigma = 1.0;  // FP32 forms: power-of-two prescale of the per-mode scale arguments
   int precision = CSL_PREC_FP64;
   int use_graph = 1;
   int use_pdl = 1;  // programmatic dependent launch of the iteration's kernels
+  int ff = 0;       // FP32-preconditioner forms: float-pair stencil (faces in cxp/cyp/czp)
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
   double *cx = nullptr, *cy = nullptr, *cz = nullptr, *dg = nullptr, *stab = nullptr;
+  float2 *cxp = nullptr, *cyp = nullptr, *czp = nullptr;
+  float2 alpha2 = {0.f, 0.f};
   double* mu_d[3] = {nullptr, nullptr, nullptr};
   float* mu_f[3] = {nullptr, nullptr, nullptr};
   void* tw[3] = {nullptr, nullptr, nullptr};
@@ -301,10 +305,13 @@ void fill_mid(csl_plan* P, StridedArgs<T>& a, int axis) {
     a.mu_col = (const T*)P->mu_f[0];
     a.mu_outer = (axis == 2) ? (const T*)P->mu_f[1] : nullptr;
   }
-  a.gamma = (T)P->gamma;
-  a.alpha = (T)P->alpha;
-  a.beta2 = (T)(P->beta * P->beta);
-  a.cnorm = (T)P->cnorm;
+  // s_k = cnorm / sqrt(e^2 + beta^2), e = gamma mu_k + alpha: every factor
+  // times sigma leaves s_k unchanged and keeps e^2 + beta^2 inside FP32 range
+  const double sg = sizeof(T) == 4 ? P->sigma : 1.0;
+  a.gamma = (T)(P->gamma * sg);
+  a.alpha = (T)(P->alpha * sg);
+  a.beta2 = (T)((P->beta * sg) * (P->beta * sg));
+  a.cnorm = (T)(P->cnorm * sg);
   a.partials = P->partials;
 }
 
@@ -337,8 +344,8 @@ cudaError_t launch_mid_chain(csl_plan* P, cudaStream_t s, DevState* st, int scal
   return launch_strided<T>(P->sy.N, P->sy.wide, false, y, P->sy.L, s);
 }
 
-template <typename T>
-cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+// stencil arguments of one plan for the buffer parity par
+StencilArgs stencil_args(const csl_plan* P, int par) {
   StencilArgs a;
   memset(&a, 0, sizeof(a));
   a.g.nx = P->n[0];
@@ -351,16 +358,36 @@ cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) 
   a.cy = P->cy;
   a.cz = P->cz;
   a.dg = P->dg;
+  a.cxp = P->cxp;
+  a.cyp = P->cyp;
+  a.czp = P->czp;
+  a.alpha2 = P->alpha2;
   a.x = P->x;
   a.b = P->b;
   a.st = P->st;
   a.partials = P->partials;
+  return a;
+}
+
+typedef void (*StencilFn)(StencilArgs, const StencilArgs*, int);
+
+// the stencil kernel for the plan's form (float pairs only with an FP32 ẑ)
+template <typename TZ>
+StencilFn stencil_fn(int dim, bool ff) {
+  if constexpr (sizeof(TZ) == 8) {
+    if (ff) return dim == 2 ? k_stencil<2, TZ, true> : k_stencil<3, TZ, true>;
+  }
+  return dim == 2 ? k_stencil<2, TZ, false> : k_stencil<3, TZ, false>;
+}
+
+template <typename T>
+cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
+  StencilArgs a = stencil_args(P, par);
   a.cond = P->cond;
   a.use_cond = use_cond ? 1 : 0;
   typedef typename C2<T>::t TZ;
   const StencilArgs* nob = nullptr;
-  if (P->dim == 2) return launch_k(P->use_pdl != 0, k_stencil<2, TZ>, P->sten_blocks, 256, 0, s, a, nob, 0);
-  return launch_k(P->use_pdl != 0, k_stencil<3, TZ>, P->sten_blocks, 256, 0, s, a, nob, 0);
+  return launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, P->ff != 0), P->sten_blocks, 256, 0, s, a, nob, 0);
 }
 
 template <typename T>
@@ -715,6 +742,7 @@ csl_status csl_plan_options_init(csl_plan_options* opt) {
   opt->use_graph = 1;
   opt->autotune = 1;
   opt->programmatic_launch = 1;
+  opt->float_pair_stencil = 1;
   return CSL_OK;
 }
 
@@ -769,6 +797,11 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   if (dim == 3) P->cz = (double*)dalloc(P, nface[2] * 8, &err);
   P->dg = (double*)dalloc(P, M * 8, &err);
   if (o.precision == CSL_PREC_FP64) P->stab = (double*)dalloc(P, M * 8, &err);
+  if (o.precision != CSL_PREC_FP64 && o.float_pair_stencil) {
+    P->cxp = (float2*)dalloc(P, nface[0] * 8, &err);
+    P->cyp = (float2*)dalloc(P, nface[1] * 8, &err);
+    if (dim == 3) P->czp = (float2*)dalloc(P, nface[2] * 8, &err);
+  }
   for (int d = 0; d < dim; ++d) {
     const int N = P->n[d] + 1;
     P->mu_d[d] = (double*)dalloc(P, (size_t)P->n[d] * 8, &err);
@@ -839,6 +872,34 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     P->amin = amin;
     P->amax = amax;
     P->gamma = (o.gamma_override > 0.0 && isfinite(o.gamma_override)) ? o.gamma_override : sqrt(amin * amax);
+    // Float-pair stencil: every scaled face, alpha and beta inside [2^-60, 2^60]
+    // (zero allowed for alpha and beta), so that both halves of each pair and
+    // their products with an FP32 ẑ stay normal floats.
+    if (P->cxp) {
+      double smin = INFINITY, smax = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        const double s2 = 1.0 / (P->h[d] * P->h[d]);
+        smin = s2 < smin ? s2 : smin;
+        smax = s2 > smax ? s2 : smax;
+      }
+      const double lo = ldexp(1.0, -60), hi = ldexp(1.0, 60);
+      auto ok_shift = [&](double v) { return v == 0.0 || (fabs(v) >= lo && fabs(v) <= hi); };
+      P->ff = (amin * smin >= lo && amax * smax <= hi && ok_shift(alpha) && ok_shift(beta)) ? 1 : 0;
+      const float ah = (float)alpha;
+      P->alpha2 = make_float2(ah, (float)(alpha - (double)ah));
+      float2* pdst[3] = {P->cxp, P->cyp, P->czp};
+      for (int d = 0; d < dim && err == cudaSuccess; ++d) {
+        const int blocks = (int)((nface[d] + 255) / 256 < 1024 ? (nface[d] + 255) / 256 : 1024);
+        k_pair_faces<<<blocks, 256, 0, s>>>(dst[d], pdst[d], nface[d]);
+        err = cudaGetLastError();
+      }
+      if (err != cudaSuccess) {
+        CSL_NOTE(err, "float-pair faces");
+        (void)cudaGetLastError();
+        free_plan(P);
+        return CSL_CUDA_ERROR;
+      }
+    }
   }
   Grid g;
   g.nx = nx;
@@ -922,6 +983,20 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       }
       P->sqrt_pmin = sqrt(sqrt(qmin));
       P->sqrt_pmax = sqrt(sqrt(qmax));
+      if (o.precision != CSL_PREC_FP64) {
+        // FP32 scale: |e + i beta| is brought to at most 2^40 when it leaves
+        // [2^-40, 2^60]; the scales s_k themselves must be normal floats
+        const double mmin = sqrt(qmin), mmax = sqrt(qmax);
+        if (mmax > ldexp(1.0, 60) || mmin < ldexp(1.0, -40)) P->sigma = ldexp(1.0, 40 - (int)ceil(log2(mmax)));
+        const double smin = P->cnorm / mmax, smax = P->cnorm / mmin;
+        if (!(smin >= ldexp(1.0, -120)) || !(smax <= ldexp(1.0, 120)) ||
+            !(mmin * P->sigma >= ldexp(1.0, -60))) {
+          csl_internal_set_error(
+              "csl_plan_create: the per-mode scales of P^-1 lie outside the FP32 range; use CSL_PREC_FP64");
+          free_plan(P);
+          return CSL_INVALID_ARG;
+        }
+      }
     }
   }
   if (err != cudaSuccess) {
@@ -1004,8 +1079,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
                         : o.precision == CSL_PREC_FP32   ? "fp32"
                         : o.precision == CSL_PREC_BF16X3 ? "bf16x3"
                                                          : "bf16x6";
-    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[blocks=%d]", pname,
-                       o.autotune ? " autotuned" : "", P->sten_blocks);
+    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[%s blocks=%d]", pname,
+                       o.autotune ? " autotuned" : "", P->ff ? "float-pair" : "fp64", P->sten_blocks);
     for (int d = 0; d < dim && off < (int)sizeof(P->config); ++d)
       off += snprintf(P->config + off, sizeof(P->config) - off, " %s[N=%d %s lines=%d threads=%d blocks=%d smem=%zu]",
                       nm[d], cs[d]->N,
@@ -1219,6 +1294,7 @@ struct BatchGroup {
   int n[3] = {1, 1, 1};
   std::vector<int> sys;  // indices of the group's systems
   csl_plan* proto = nullptr;
+  int ff = 1;  // all systems of the group take the float-pair stencil
   StencilArgs* d_sten[2] = {nullptr, nullptr};
   void* d_p1[2] = {nullptr, nullptr};   // RowArgs<T>
   void* d_p3[2] = {nullptr, nullptr};   // RowArgs<T>
@@ -1323,24 +1399,10 @@ cudaError_t build_group_args(csl_batch* B, BatchGroup& G) {
     std::vector<RowArgs<T>> p1(ns), p3(ns);
     for (int i = 0; i < ns; ++i) {
       csl_plan* P = B->plans[G.sys[i]];
-      StencilArgs a;
-      memset(&a, 0, sizeof(a));
-      a.g.nx = P->n[0];
-      a.g.ny = P->n[1];
-      a.g.nz = P->dim == 3 ? P->n[2] : 1;
-      a.g.M = P->M;
-      a.z = P->z[par];
-      a.vold = P->v[1 - par];
-      a.cx = P->cx;
-      a.cy = P->cy;
-      a.cz = P->cz;
-      a.dg = P->dg;
-      a.x = P->x;
-      a.b = P->b;
-      a.st = P->st;
-      a.partials = P->partials;
+      StencilArgs a = stencil_args(P, par);
       a.use_cond = 0;
       sa[i] = a;
+      if (!P->ff) G.ff = 0;
       p1[i] = p1_args<T>(P, par);
       p3[i] = p3_args<T>(P, par);
     }
@@ -1426,9 +1488,8 @@ cudaError_t group_iteration(csl_batch* B, BatchGroup& G, int par, cudaStream_t s
   StencilArgs sd;
   memset(&sd, 0, sizeof(sd));
   const StencilArgs* sb = (const StencilArgs*)G.d_sten[par];
-  cudaError_t e =
-      P->dim == 2 ? launch_k(P->use_pdl != 0, k_stencil<2, TZ>, P->sten_blocks * ns, 256, 0, s, sd, sb, P->sten_blocks)
-                  : launch_k(P->use_pdl != 0, k_stencil<3, TZ>, P->sten_blocks * ns, 256, 0, s, sd, sb, P->sten_blocks);
+  cudaError_t e = launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, G.ff != 0), P->sten_blocks * ns, 256, 0, s, sd,
+                           sb, P->sten_blocks);
   RowArgs<T> rd;
   memset(&rd, 0, sizeof(rd));
   if (e == cudaSuccess)

@@ -101,6 +101,10 @@ struct StencilArgs {
   const double* cy;
   const double* cz;
   const double* dg;
+  const float2* cxp;      // the same faces as float pairs (FF path): c = hi + lo
+  const float2* cyp;
+  const float2* czp;
+  float2 alpha2;          // alpha as a float pair
   const double2* x;       // current iterate (true-residual check)
   const double2* b;       // right-hand side (block form)
   DevState* st;
@@ -108,6 +112,68 @@ struct StencilArgs {
   cudaGraphConditionalHandle cond;
   int use_cond;
 };
+
+// ---------------------------------------------------------------------------
+// Float-pair ("double-float") arithmetic for the stencil of the FP32-
+// preconditioner forms.  A value is the unevaluated sum h + l of two floats.
+// GB300 issues FP32 at 64 times its FP64 rate, so a pair product-sum of about
+// 18 FP32 instructions costs less issue time than one FP64 FMA costs FP64
+// pipe time.  The sums are error-free transformations (Knuth's TwoSum and the
+// FMA product error), rounded to nearest with no contraction; the pair keeps
+// about 2^-47 relative accuracy, which the difference form below spends on
+// small terms.
+// ---------------------------------------------------------------------------
+struct ff2 {
+  float h, l;
+};
+
+// a + b exactly, as s + e (Knuth's TwoSum, no ordering condition)
+__device__ __forceinline__ ff2 ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// acc += p, p = ph + pl: the high parts summed exactly, the low parts in FP32
+__device__ __forceinline__ void ff_acc(ff2& acc, float ph, float pl) {
+  const ff2 t = ff_two_sum(acc.h, ph);
+  acc.h = t.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(pl, t.l));
+}
+
+// c * x for a pair c and a float x (c.h * x exactly via its FMA error term)
+__device__ __forceinline__ ff2 ff_mul1(float2 c, float x) {
+  const float ph = __fmul_rn(c.x, x);
+  return {ph, __fmaf_rn(c.y, x, __fmaf_rn(c.x, x, -ph))};
+}
+
+// acc += c * x
+__device__ __forceinline__ void ff_acc_mul1(ff2& acc, float2 c, float x) {
+  const ff2 p = ff_mul1(c, x);
+  ff_acc(acc, p.h, p.l);
+}
+
+// acc += c * (zc - zq) for one component: the difference of the two floats is
+// formed exactly, then multiplied by the pair c (the c.l * d.l term, below
+// 2^-47 of the product, is dropped)
+__device__ __forceinline__ void ff_acc_flux(ff2& acc, float2 c, float zc, float zq) {
+  const ff2 d = ff_two_sum(zc, -zq);
+  const float ph = __fmul_rn(c.x, d.h);
+  float pl = __fmaf_rn(c.x, d.h, -ph);
+  pl = __fmaf_rn(c.x, d.l, pl);
+  pl = __fmaf_rn(c.y, d.h, pl);
+  ff_acc(acc, ph, pl);
+}
+
+__device__ __forceinline__ double ff_to_d(ff2 v) { return f2d_exact(v.h) + f2d_exact(v.l); }
+
+__device__ __forceinline__ float2 shfl_up_f2(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_down_f2(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
 
 // Rows (2D) or planes (3D) one warp walks per strip of the stencil kernel.
 constexpr int kStencilStrip = 16;
@@ -237,9 +303,55 @@ struct StepOperands {
   }
 };
 
-// batch: optional per-system argument array (system = blockIdx.x / bps)
-template <int DIM, typename TZ>
+// Operands of one step of a strip for the float-pair stencil (ẑ in FP32):
+// as StepOperands, with the faces as float pairs and no diagonal.
+template <int DIM>
+struct FFOperands {
+  float2 zn1, zl, zr, ys, yn;
+  float2 cw, ce, cs, cn, cd, cu;
+  double2 vo;
+  __device__ __forceinline__ void load(const float2* z, const StencilArgs& a, long p, long mstride, int m, int nm,
+                                       int x, int yfix, bool vx, int lane) {
+    const int nx = a.g.nx, ny = a.g.ny;
+    const float2 zero = make_float2(0.f, 0.f);
+    zn1 = (vx && m + 1 < nm) ? z[p + mstride] : zero;
+    zl = (lane == 0 && vx && x > 0) ? z[p - 1] : zero;
+    zr = (lane == 31 && x + 1 < nx) ? z[p + 1] : zero;
+    cw = ce = cs = cn = cd = cu = zero;
+    vo = make_double2(0.0, 0.0);
+    ys = yn = zero;
+    if (vx) {
+      long rx, ry;
+      if (DIM == 2) {
+        rx = (long)m * (nx + 1) + x;
+        ry = (long)m * nx + x;
+      } else {
+        rx = ((long)m * ny + yfix) * (nx + 1) + x;
+        ry = ((long)m * (ny + 1) + yfix) * nx + x;
+        if (yfix > 0) ys = z[p - nx];
+        if (yfix < ny - 1) yn = z[p + nx];
+        cd = a.czp[p];
+        cu = a.czp[p + mstride];
+      }
+      cw = a.cxp[rx];
+      ce = a.cxp[rx + 1];
+      cs = a.cyp[ry];
+      cn = a.cyp[ry + nx];
+      vo = a.vold[p];
+    }
+  }
+};
+
+// batch: optional per-system argument array (system = blockIdx.x / bps).
+// FF (FP32 ẑ only): the non-checking steps form (K + alpha I) ẑ in the
+// difference form alpha z_p + sum_e c_e (z_p - z_q) of Eq. 1 in float-pair
+// arithmetic (the differences of neighbouring values are exact and small, so
+// the large cancelling terms c_e z_p of the direct form never appear), add the
+// beta block term and delta in pairs, and leave 4 FP64 operations per point
+// (u' = A ẑ - lanc v_{j-1} against the FP64 Lanczos vector).
+template <int DIM, typename TZ, bool FF>
 __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
+  static_assert(!FF || sizeof(TZ) == 8, "the float-pair stencil reads an FP32 z");
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
   const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
   const int nblk = batch ? bps : (int)gridDim.x;
@@ -263,6 +375,12 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
   const long nsx = (nx + 31) / 32, nsm = (nm + kStencilStrip - 1) / kStencilStrip;
   const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz);
   double acc[2] = {0.0, 0.0};
+  ff2 dacc = {0.f, 0.f};
+  float2 beta2 = make_float2(0.f, 0.f);
+  if (FF) {
+    const float bh = d2f_rn(beta);
+    beta2 = make_float2(bh, d2f_rn(beta - f2d_exact(bh)));
+  }
   for (long s = (long)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
        s += (long)nblk * (blockDim.x >> 5)) {
     const int sx = (int)(s % nsx);
@@ -272,6 +390,56 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
     const bool vx = x < nx;
     const int m0 = sm * kStencilStrip, m1 = min(m0 + kStencilStrip, nm);
     const long base = DIM == 2 ? (long)x : (long)yfix * nx + x;
+    if (FF && !check) {
+      const float2* zf = (const float2*)a.z;
+      const float2 zero = make_float2(0.f, 0.f);
+      const float2 nbeta2 = make_float2(-beta2.x, -beta2.y);
+      float2 zm = (vx && m0 > 0) ? zf[base + (long)(m0 - 1) * mstride] : zero;
+      float2 zc = vx ? zf[base + (long)m0 * mstride] : zero;
+      FFOperands<DIM> cur, nxt;
+      cur.load(zf, a, base + (long)m0 * mstride, mstride, m0, nm, x, yfix, vx, lane);
+      for (int m = m0; m < m1; ++m) {
+        const long p = base + (long)m * mstride;
+        if (m + 1 < m1) nxt.load(zf, a, p + mstride, mstride, m + 1, nm, x, yfix, vx, lane);
+        const float2 zp = cur.zn1;
+        float2 zl = shfl_up_f2(zc), zr = shfl_down_f2(zc);
+        if (lane == 0) zl = cur.zl;
+        if (lane == 31) zr = cur.zr;
+        if (vx) {
+          ff2 kx = ff_mul1(a.alpha2, zc.x), ky = ff_mul1(a.alpha2, zc.y);
+          ff_acc_flux(kx, cur.cw, zc.x, zl.x);
+          ff_acc_flux(ky, cur.cw, zc.y, zl.y);
+          ff_acc_flux(kx, cur.ce, zc.x, zr.x);
+          ff_acc_flux(ky, cur.ce, zc.y, zr.y);
+          if (DIM == 2) {
+            ff_acc_flux(kx, cur.cs, zc.x, zm.x);
+            ff_acc_flux(ky, cur.cs, zc.y, zm.y);
+            ff_acc_flux(kx, cur.cn, zc.x, zp.x);
+            ff_acc_flux(ky, cur.cn, zc.y, zp.y);
+          } else {
+            ff_acc_flux(kx, cur.cs, zc.x, cur.ys.x);
+            ff_acc_flux(ky, cur.cs, zc.y, cur.ys.y);
+            ff_acc_flux(kx, cur.cn, zc.x, cur.yn.x);
+            ff_acc_flux(ky, cur.cn, zc.y, cur.yn.y);
+            ff_acc_flux(kx, cur.cd, zc.x, zm.x);
+            ff_acc_flux(ky, cur.cd, zc.y, zm.y);
+            ff_acc_flux(kx, cur.cu, zc.x, zp.x);
+            ff_acc_flux(ky, cur.cu, zc.y, zp.y);
+          }
+          // block row of Eq. 2: (A z).x = beta z1 + (K+alpha) z2 in ky, (A z).y in kx
+          ff_acc_mul1(ky, beta2, zc.x);
+          ff_acc_mul1(kx, nbeta2, zc.y);
+          ff_acc_mul1(dacc, make_float2(ky.h, ky.l), zc.x);
+          ff_acc_mul1(dacc, make_float2(kx.h, kx.l), zc.y);
+          a.vold[p] = make_double2(fma(-lanc, cur.vo.x, f2d_exact(ky.h)) + f2d_exact(ky.l),
+                                   fma(-lanc, cur.vo.y, f2d_exact(kx.h)) + f2d_exact(kx.l));
+        }
+        zm = zc;
+        zc = zp;
+        cur = nxt;
+      }
+      continue;
+    }
     if (!check) {
       // u' = A z - lanc v_{j-1} and delta, operands of step m+1 loaded
       // before step m computes
@@ -345,6 +513,7 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
       if (check) wx.advance();
     }
   }
+  if (FF) acc[0] += ff_to_d(dacc);
   pdl_trigger();
   double tot[2];
   if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot, bid, nblk)) return;
@@ -541,6 +710,15 @@ static __global__ void k_scale_faces(const double* __restrict__ src, double* __r
   atomicMin(&minmax[0], lmin);
   atomicMax(&minmax[1], lmax);
   if (bad) atomicOr(&minmax[2], 1ull);
+}
+
+// scaled faces as float pairs for the float-pair stencil: hi = RN(c), lo = RN(c - hi)
+static __global__ void k_pair_faces(const double* __restrict__ c, float2* __restrict__ out, long count) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const double v = c[i];
+    const float h = __double2float_rn(v);
+    out[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
 }
 
 // diagonal of K + alpha I: sum of the (scaled) face coefficients of p, + alpha

@@ -257,10 +257,11 @@ __device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, 
   DevState* st = a.st;
   if (a.scalar_mode == 1) {
     const double g2 = tot[0];
+    // f = 0 never reaches this pass (the ingest closes the solve with z = 0),
+    // so <P^{-1} r0, r0> = 0 for a positive definite P is an underflow
     if (!(g2 > 0.0) || !(g2 < 1e300)) {
       st->done = 1;
-      st->status = (g2 == 0.0) ? ST_OK : ST_BREAKDOWN;
-      st->relres = (g2 == 0.0) ? 0.0 : st->relres;
+      st->status = ST_BREAKDOWN;
       return;
     }
     st->gam = sqrt(g2);
