@@ -136,6 +136,7 @@ struct csl_plan {
   unsigned long long* u64 = nullptr;
   PassCfg row, sy, sz;
   int sten_blocks = 1, ew_blocks = 1;
+  int sten_strip = kStencilStrip;  // steps per warp strip of the stencil
   double cnorm = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -362,6 +363,7 @@ StencilArgs stencil_args(const csl_plan* P, int par) {
   a.cyp = P->cyp;
   a.czp = P->czp;
   a.alpha2 = P->alpha2;
+  a.strip = P->sten_strip;
   a.x = P->x;
   a.b = P->b;
   a.st = P->st;
@@ -387,7 +389,8 @@ cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) 
   a.use_cond = use_cond ? 1 : 0;
   typedef typename C2<T>::t TZ;
   const StencilArgs* nob = nullptr;
-  return launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, P->ff != 0), P->sten_blocks, 256, 0, s, a, nob, 0);
+  const size_t smem = (sizeof(TZ) == 8 && P->ff) ? ff_stencil_smem(P->dim) : 0;
+  return launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, P->ff != 0), P->sten_blocks, 256, smem, s, a, nob, 0);
 }
 
 template <typename T>
@@ -831,11 +834,6 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   cudaStream_t s = P->stream;
   P->ew_blocks = (int)((M + 255) / 256 < kSMs * 8 ? (M + 255) / 256 : kSMs * 8);
-  {
-    const long strips = stencil_strips(dim, nx, ny, nz);  // one warp per strip, 8 warps per CTA
-    const long blocks = (strips + 7) / 8;
-    P->sten_blocks = (int)(blocks < kSMs * 8 ? blocks : kSMs * 8);
-  }
 
   // coefficient faces: a_e / h^2, min / max / validity (Eq. 1 and Eq. 4's a_min, a_max)
   {
@@ -888,6 +886,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       const float ah = (float)alpha;
       P->alpha2 = make_float2(ah, (float)(alpha - (double)ah));
       float2* pdst[3] = {P->cxp, P->cyp, P->czp};
+      if (P->ff) err = allow_dyn_smem((const void*)stencil_fn<float2>(dim, true));
       for (int d = 0; d < dim && err == cudaSuccess; ++d) {
         const int blocks = (int)((nface[d] + 255) / 256 < 1024 ? (nface[d] + 255) / 256 : 1024);
         k_pair_faces<<<blocks, 256, 0, s>>>(dst[d], pdst[d], nface[d]);
@@ -900,6 +899,12 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
         return CSL_CUDA_ERROR;
       }
     }
+  }
+  {
+    // one warp per strip, 8 warps per CTA
+    P->sten_strip = P->ff ? strip_rows(dim, nx, ny, nz, kSMs) : kStencilStrip;
+    const long blocks = (stencil_strips(dim, nx, ny, nz, P->sten_strip) + 7) / 8;
+    P->sten_blocks = (int)(blocks < kSMs * 8 ? blocks : kSMs * 8);
   }
   Grid g;
   g.nx = nx;
@@ -1079,8 +1084,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
                         : o.precision == CSL_PREC_FP32   ? "fp32"
                         : o.precision == CSL_PREC_BF16X3 ? "bf16x3"
                                                          : "bf16x6";
-    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[%s blocks=%d]", pname,
-                       o.autotune ? " autotuned" : "", P->ff ? "float-pair" : "fp64", P->sten_blocks);
+    int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[%s strip=%d blocks=%d]", pname,
+                       o.autotune ? " autotuned" : "", P->ff ? "float-pair" : "fp64", P->sten_strip, P->sten_blocks);
     for (int d = 0; d < dim && off < (int)sizeof(P->config); ++d)
       off += snprintf(P->config + off, sizeof(P->config) - off, " %s[N=%d %s lines=%d threads=%d blocks=%d smem=%zu]",
                       nm[d], cs[d]->N,
@@ -1488,8 +1493,9 @@ cudaError_t group_iteration(csl_batch* B, BatchGroup& G, int par, cudaStream_t s
   StencilArgs sd;
   memset(&sd, 0, sizeof(sd));
   const StencilArgs* sb = (const StencilArgs*)G.d_sten[par];
-  cudaError_t e = launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, G.ff != 0), P->sten_blocks * ns, 256, 0, s, sd,
-                           sb, P->sten_blocks);
+  const size_t smem = (sizeof(TZ) == 8 && G.ff) ? ff_stencil_smem(P->dim) : 0;
+  cudaError_t e = launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, G.ff != 0), P->sten_blocks * ns, 256, smem, s,
+                           sd, sb, P->sten_blocks);
   RowArgs<T> rd;
   memset(&rd, 0, sizeof(rd));
   if (e == cudaSuccess)

@@ -105,6 +105,7 @@ struct StencilArgs {
   const float2* cyp;
   const float2* czp;
   float2 alpha2;          // alpha as a float pair
+  int strip;              // steps per warp strip along the marching axis
   const double2* x;       // current iterate (true-residual check)
   const double2* b;       // right-hand side (block form)
   DevState* st;
@@ -154,19 +155,37 @@ __device__ __forceinline__ void ff_acc_mul1(ff2& acc, float2 c, float x) {
   ff_acc(acc, p.h, p.l);
 }
 
-// acc += c * (zc - zq) for one component: the difference of the two floats is
-// formed exactly, then multiplied by the pair c (the c.l * d.l term, below
-// 2^-47 of the product, is dropped)
-__device__ __forceinline__ void ff_acc_flux(ff2& acc, float2 c, float zc, float zq) {
+// The flux c * (zc - zq) across one face for one component, as a pair: the
+// difference of the two floats is formed exactly, then multiplied by the
+// pair c (the c.l * d.l term, below 2^-47 of the product, is dropped)
+__device__ __forceinline__ ff2 ff_flux(float2 c, float zc, float zq) {
   const ff2 d = ff_two_sum(zc, -zq);
   const float ph = __fmul_rn(c.x, d.h);
   float pl = __fmaf_rn(c.x, d.h, -ph);
   pl = __fmaf_rn(c.x, d.l, pl);
   pl = __fmaf_rn(c.y, d.h, pl);
-  ff_acc(acc, ph, pl);
+  return {ph, pl};
+}
+
+// acc += c * (zc - zq)
+__device__ __forceinline__ void ff_acc_flux(ff2& acc, float2 c, float zc, float zq) {
+  const ff2 f = ff_flux(c, zc, zq);
+  ff_acc(acc, f.h, f.l);
 }
 
 __device__ __forceinline__ double ff_to_d(ff2 v) { return f2d_exact(v.h) + f2d_exact(v.l); }
+
+// float -> double by field moves without branches, for the halves of a pair
+// on their way into an FP64 vector: normal floats, zeros, infinities and NaN
+// convert exactly; a subnormal float (|f| < 2^-126) becomes a signed zero.
+__device__ __forceinline__ double f2d_ftz(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned ex = e == 255u ? 0x7ffu : e + 896u;
+  const unsigned hi = (u & 0x80000000u) | (ex << 20) | ((u >> 3) & 0xfffffu);
+  const bool z = e == 0u;
+  return __hiloint2double((int)(z ? (u & 0x80000000u) : hi), (int)(z ? 0u : (u << 29)));
+}
 
 __device__ __forceinline__ float2 shfl_up_f2(float2 v) {
   return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
@@ -175,7 +194,8 @@ __device__ __forceinline__ float2 shfl_down_f2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
-// Rows (2D) or planes (3D) one warp walks per strip of the stencil kernel.
+// Rows (2D) or planes (3D) one warp walks per strip of the FP64-arithmetic
+// stencil; the float-pair stencil sizes its strips per plan (strip_rows).
 constexpr int kStencilStrip = 16;
 
 __device__ __forceinline__ double2 shfl_up_d2(double2 v) {
@@ -185,12 +205,24 @@ __device__ __forceinline__ double2 shfl_down_d2(double2 v) {
   return make_double2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
-// Number of warp strips of k_stencil (32 x-columns by kStencilStrip steps
-// along the marching axis: y in 2D, z in 3D).
-__host__ __device__ inline long stencil_strips(int dim, int nx, int ny, int nz) {
+// Number of warp strips of k_stencil (32 x-columns by `strip` steps along
+// the marching axis: y in 2D, z in 3D).
+__host__ __device__ inline long stencil_strips(int dim, int nx, int ny, int nz, int strip) {
   const long nsx = (nx + 31) / 32;
   const long nm = dim == 2 ? ny : nz;
-  return nsx * ((nm + kStencilStrip - 1) / kStencilStrip) * (dim == 3 ? ny : 1);
+  return nsx * ((nm + strip - 1) / strip) * (dim == 3 ? ny : 1);
+}
+
+// Strip length of the float-pair stencil: enough strips for 24 warps on each
+// of the 152 SMs (three 8-warp CTAs at 80 registers), so that the dependent
+// pair arithmetic of one warp hides behind the others; 4 .. 64 steps.
+inline int strip_rows(int dim, int nx, int ny, int nz, int sms) {
+  const long cols = (long)((nx + 31) / 32) * (dim == 3 ? ny : 1);
+  const long nm = dim == 2 ? ny : nz;
+  long per_col = (long)sms * 24 / cols;
+  if (per_col < 1) per_col = 1;
+  const long strip = (nm + per_col - 1) / per_col;
+  return (int)(strip < 4 ? 4 : strip > 64 ? 64 : strip);
 }
 
 // One value of a strip and its marching window: m-1, m, m+1 along the strip,
@@ -303,44 +335,49 @@ struct StepOperands {
   }
 };
 
-// Operands of one step of a strip for the float-pair stencil (ẑ in FP32):
-// as StepOperands, with the faces as float pairs and no diagonal.
+// Asynchronous global -> shared copies (cp.async) of 8 or 16 bytes; a false
+// predicate copies nothing and zero-fills the destination (the source is
+// then not read, and callers pass a valid address anyway).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Float-pair stencil: one stage of a warp's operand ring holds what step m of
+// its strip needs beyond the values carried from step m-1 (ẑ at m-1 and m,
+// in 2D the south face = the previous north face, in 3D the lower z-face =
+// the previous upper one).  cw[32] is the east face of lane 31; edge[0] and
+// edge[1] are the x-neighbours of lanes 0 and 31 from outside the strip.
+constexpr int kFFStages = 4;
 template <int DIM>
-struct FFOperands {
-  float2 zn1, zl, zr, ys, yn;
-  float2 cw, ce, cs, cn, cd, cu;
-  double2 vo;
-  __device__ __forceinline__ void load(const float2* z, const StencilArgs& a, long p, long mstride, int m, int nm,
-                                       int x, int yfix, bool vx, int lane) {
-    const int nx = a.g.nx, ny = a.g.ny;
-    const float2 zero = make_float2(0.f, 0.f);
-    zn1 = (vx && m + 1 < nm) ? z[p + mstride] : zero;
-    zl = (lane == 0 && vx && x > 0) ? z[p - 1] : zero;
-    zr = (lane == 31 && x + 1 < nx) ? z[p + 1] : zero;
-    cw = ce = cs = cn = cd = cu = zero;
-    vo = make_double2(0.0, 0.0);
-    ys = yn = zero;
-    if (vx) {
-      long rx, ry;
-      if (DIM == 2) {
-        rx = (long)m * (nx + 1) + x;
-        ry = (long)m * nx + x;
-      } else {
-        rx = ((long)m * ny + yfix) * (nx + 1) + x;
-        ry = ((long)m * (ny + 1) + yfix) * nx + x;
-        if (yfix > 0) ys = z[p - nx];
-        if (yfix < ny - 1) yn = z[p + nx];
-        cd = a.czp[p];
-        cu = a.czp[p + mstride];
-      }
-      cw = a.cxp[rx];
-      ce = a.cxp[rx + 1];
-      cs = a.cyp[ry];
-      cn = a.cyp[ry + nx];
-      vo = a.vold[p];
-    }
-  }
+struct FFStage {
+  double2 v[32];     // v_{j-1} at the step's points
+  float2 zp[32];     // ẑ at m+1
+  float2 cn[32];     // y-face above the point
+  float2 cw[33];     // x-face left of the point (+ lane 31's right face)
+  float2 edge[2];
+  float2 cs[DIM == 3 ? 32 : 1];  // 3D: y-face below (2D carries it)
+  float2 ys[DIM == 3 ? 32 : 1];  // 3D: y-neighbours
+  float2 yn[DIM == 3 ? 32 : 1];
+  float2 cu[DIM == 3 ? 32 : 1];  // 3D: z-face above
 };
+template <int DIM>
+__host__ __device__ constexpr int ff_stage_bytes() {
+  return (int)((sizeof(FFStage<DIM>) + 15) / 16 * 16);
+}
+// dynamic shared memory of one 256-thread float-pair stencil CTA
+__host__ __device__ constexpr int ff_stencil_smem(int dim) {
+  return 8 * kFFStages * (dim == 2 ? ff_stage_bytes<2>() : ff_stage_bytes<3>());
+}
 
 // batch: optional per-system argument array (system = blockIdx.x / bps).
 // FF (FP32 ẑ only): the non-checking steps form (K + alpha I) ẑ in the
@@ -350,7 +387,7 @@ struct FFOperands {
 // beta block term and delta in pairs, and leave 4 FP64 operations per point
 // (u' = A ẑ - lanc v_{j-1} against the FP64 Lanczos vector).
 template <int DIM, typename TZ, bool FF>
-__global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
+__global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
   static_assert(!FF || sizeof(TZ) == 8, "the float-pair stencil reads an FP32 z");
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
   const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
@@ -372,8 +409,9 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
   const int nm = DIM == 2 ? a.g.ny : a.g.nz;
   const long mstride = DIM == 2 ? (long)nx : (long)nx * ny;
   const int lane = threadIdx.x & 31;
-  const long nsx = (nx + 31) / 32, nsm = (nm + kStencilStrip - 1) / kStencilStrip;
-  const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz);
+  const int strip = a.strip;
+  const long nsx = (nx + 31) / 32, nsm = (nm + strip - 1) / strip;
+  const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz, strip);
   double acc[2] = {0.0, 0.0};
   ff2 dacc = {0.f, 0.f};
   float2 beta2 = make_float2(0.f, 0.f);
@@ -388,56 +426,113 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs a0, const StencilAr
     const int yfix = DIM == 3 ? (int)(s / (nsx * nsm)) : 0;
     const int x = sx * 32 + lane;
     const bool vx = x < nx;
-    const int m0 = sm * kStencilStrip, m1 = min(m0 + kStencilStrip, nm);
+    const int m0 = sm * strip, m1 = min(m0 + strip, nm);
     const long base = DIM == 2 ? (long)x : (long)yfix * nx + x;
     if (FF && !check) {
+      // Operands stream through the warp's ring of kFFStages stages, filled
+      // kFFStages - 1 steps ahead by cp.async; ẑ at m-1 and m and the faces
+      // shared with the previous step are carried in registers.
       const float2* zf = (const float2*)a.z;
       const float2 zero = make_float2(0.f, 0.f);
       const float2 nbeta2 = make_float2(-beta2.x, -beta2.y);
-      float2 zm = (vx && m0 > 0) ? zf[base + (long)(m0 - 1) * mstride] : zero;
-      float2 zc = vx ? zf[base + (long)m0 * mstride] : zero;
-      FFOperands<DIM> cur, nxt;
-      cur.load(zf, a, base + (long)m0 * mstride, mstride, m0, nm, x, yfix, vx, lane);
-      for (int m = m0; m < m1; ++m) {
+      extern __shared__ __align__(16) unsigned char ff_ring[];
+      unsigned char* ring = ff_ring + (size_t)(threadIdx.x >> 5) * kFFStages * ff_stage_bytes<DIM>();
+      const int nsteps = m1 - m0;
+      auto issue = [&](int m, int slot) {
+        FFStage<DIM>& S = *(FFStage<DIM>*)(ring + slot * ff_stage_bytes<DIM>());
         const long p = base + (long)m * mstride;
-        if (m + 1 < m1) nxt.load(zf, a, p + mstride, mstride, m + 1, nm, x, yfix, vx, lane);
-        const float2 zp = cur.zn1;
+        long rx, ry;
+        if (DIM == 2) {
+          rx = (long)m * (nx + 1) + x;
+          ry = (long)m * nx + x;
+        } else {
+          rx = ((long)m * ny + yfix) * (nx + 1) + x;
+          ry = ((long)m * (ny + 1) + yfix) * nx + x;
+        }
+        cp_async16(&S.v[lane], vx ? (const void*)(a.vold + p) : (const void*)a.vold, vx);
+        const bool hz = vx && m + 1 < nm;
+        cp_async8(&S.zp[lane], hz ? zf + p + mstride : zf, hz);
+        cp_async8(&S.cn[lane], vx ? a.cyp + ry + nx : a.cyp, vx);
+        const bool hw = x <= nx;  // the face left of column x exists for x = nx too
+        cp_async8(&S.cw[lane], hw ? a.cxp + rx : a.cxp, hw);
+        if (lane == 31) cp_async8(&S.cw[32], vx ? a.cxp + rx + 1 : a.cxp, vx);
+        if (lane == 0) cp_async8(&S.edge[0], (vx && x > 0) ? zf + p - 1 : zf, vx && x > 0);
+        if (lane == 31) cp_async8(&S.edge[1], (x + 1 < nx) ? zf + p + 1 : zf, x + 1 < nx);
+        if (DIM == 3) {
+          cp_async8(&S.cs[lane], vx ? a.cyp + ry : a.cyp, vx);
+          const bool hs = vx && yfix > 0, hn = vx && yfix < ny - 1;
+          cp_async8(&S.ys[lane], hs ? zf + p - nx : zf, hs);
+          cp_async8(&S.yn[lane], hn ? zf + p + nx : zf, hn);
+          cp_async8(&S.cu[lane], vx ? a.czp + p + mstride : a.czp, vx);
+        }
+      };
+      // prologue: stages for steps m0 .. m0 + kFFStages - 2 (one group each,
+      // empty groups past the strip's end keep the group count uniform)
+#pragma unroll
+      for (int k = 0; k < kFFStages - 1; ++k) {
+        if (k < nsteps) issue(m0 + k, k);
+        cp_async_commit();
+      }
+      const long p0 = base + (long)m0 * mstride;
+      float2 zm = (vx && m0 > 0) ? zf[p0 - mstride] : zero;
+      float2 zc = vx ? zf[p0] : zero;
+      // flux across the face below the point along the marching axis, carried
+      // from the step before as minus its flux across the face above
+      ff2 fbx = {0.f, 0.f}, fby = {0.f, 0.f};
+      if (vx) {
+        const float2 cb = DIM == 2 ? a.cyp[(long)m0 * nx + x] : a.czp[p0];
+        fbx = ff_flux(cb, zc.x, zm.x);
+        fby = ff_flux(cb, zc.y, zm.y);
+      }
+      for (int i = 0; i < nsteps; ++i) {
+        const int m = m0 + i;
+        const long p = base + (long)m * mstride;
+        if (i + kFFStages - 1 < nsteps) issue(m + kFFStages - 1, (i + kFFStages - 1) % kFFStages);
+        cp_async_commit();
+        cp_async_wait<kFFStages - 1>();
+        __syncwarp();
+        const FFStage<DIM>& S = *(const FFStage<DIM>*)(ring + (i % kFFStages) * ff_stage_bytes<DIM>());
+        const float2 zp = S.zp[lane];
         float2 zl = shfl_up_f2(zc), zr = shfl_down_f2(zc);
-        if (lane == 0) zl = cur.zl;
-        if (lane == 31) zr = cur.zr;
+        if (lane == 0) zl = S.edge[0];
+        if (lane == 31) zr = S.edge[1];
+        const float2 cw = S.cw[lane], ce = S.cw[lane + 1];
+        const float2 ca = DIM == 2 ? S.cn[lane] : S.cu[lane];  // face above along the marching axis
         if (vx) {
           ff2 kx = ff_mul1(a.alpha2, zc.x), ky = ff_mul1(a.alpha2, zc.y);
-          ff_acc_flux(kx, cur.cw, zc.x, zl.x);
-          ff_acc_flux(ky, cur.cw, zc.y, zl.y);
-          ff_acc_flux(kx, cur.ce, zc.x, zr.x);
-          ff_acc_flux(ky, cur.ce, zc.y, zr.y);
-          if (DIM == 2) {
-            ff_acc_flux(kx, cur.cs, zc.x, zm.x);
-            ff_acc_flux(ky, cur.cs, zc.y, zm.y);
-            ff_acc_flux(kx, cur.cn, zc.x, zp.x);
-            ff_acc_flux(ky, cur.cn, zc.y, zp.y);
-          } else {
-            ff_acc_flux(kx, cur.cs, zc.x, cur.ys.x);
-            ff_acc_flux(ky, cur.cs, zc.y, cur.ys.y);
-            ff_acc_flux(kx, cur.cn, zc.x, cur.yn.x);
-            ff_acc_flux(ky, cur.cn, zc.y, cur.yn.y);
-            ff_acc_flux(kx, cur.cd, zc.x, zm.x);
-            ff_acc_flux(ky, cur.cd, zc.y, zm.y);
-            ff_acc_flux(kx, cur.cu, zc.x, zp.x);
-            ff_acc_flux(ky, cur.cu, zc.y, zp.y);
+          ff_acc_flux(kx, cw, zc.x, zl.x);
+          ff_acc_flux(ky, cw, zc.y, zl.y);
+          ff_acc_flux(kx, ce, zc.x, zr.x);
+          ff_acc_flux(ky, ce, zc.y, zr.y);
+          ff_acc(kx, fbx.h, fbx.l);
+          ff_acc(ky, fby.h, fby.l);
+          const ff2 fax = ff_flux(ca, zc.x, zp.x), fay = ff_flux(ca, zc.y, zp.y);
+          ff_acc(kx, fax.h, fax.l);
+          ff_acc(ky, fay.h, fay.l);
+          fbx = {-fax.h, -fax.l};
+          fby = {-fay.h, -fay.l};
+          if (DIM == 3) {
+            const float2 cs = S.cs[lane], cn = S.cn[lane], ys = S.ys[lane], yn = S.yn[lane];
+            ff_acc_flux(kx, cs, zc.x, ys.x);
+            ff_acc_flux(ky, cs, zc.y, ys.y);
+            ff_acc_flux(kx, cn, zc.x, yn.x);
+            ff_acc_flux(ky, cn, zc.y, yn.y);
           }
           // block row of Eq. 2: (A z).x = beta z1 + (K+alpha) z2 in ky, (A z).y in kx
           ff_acc_mul1(ky, beta2, zc.x);
           ff_acc_mul1(kx, nbeta2, zc.y);
           ff_acc_mul1(dacc, make_float2(ky.h, ky.l), zc.x);
           ff_acc_mul1(dacc, make_float2(kx.h, kx.l), zc.y);
-          a.vold[p] = make_double2(fma(-lanc, cur.vo.x, f2d_exact(ky.h)) + f2d_exact(ky.l),
-                                   fma(-lanc, cur.vo.y, f2d_exact(kx.h)) + f2d_exact(kx.l));
+          const double2 vo = S.v[lane];
+          a.vold[p] = make_double2(fma(-lanc, vo.x, f2d_ftz(ky.h)) + f2d_ftz(ky.l),
+                                   fma(-lanc, vo.y, f2d_ftz(kx.h)) + f2d_ftz(kx.l));
         }
+        __syncwarp();  // every lane is done with this slot before it is refilled
         zm = zc;
         zc = zp;
-        cur = nxt;
       }
+      cp_async_wait<0>();
+      __syncwarp();
       continue;
     }
     if (!check) {
