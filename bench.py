@@ -178,6 +178,15 @@ def kernel_model(name, M, d, prec, N, ff=False):
             f64 += dst_flops
         else:
             f32 += dst_flops
+    elif name.startswith("k_row<LOAD_T,STORE_Z>"):  # inverse x transform only (update split off)
+        b = 2 * sT
+        if prec == "fp64":
+            f64 += dst_flops
+        else:
+            f32 += dst_flops
+    elif name == "k_update":  # w_{j+1}, x_j: z_j, w_{j-1}, w_j, x in; w_{j+1}, x out
+        b = sT + 80
+        f64 = 12
     elif name == "k_strided<mid>":
         b = 2 * sT + (8 if prec == "fp64" else 0)
         fl = 2 * dst_flops + 7

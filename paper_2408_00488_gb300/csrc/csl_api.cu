@@ -113,6 +113,12 @@ struct csl_plan {
   int ff = 0;       // FP32-preconditioner forms: float-pair stencil (faces in cxp/cyp/czp)
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
+  // the w/x update of an iteration runs on a side branch beside the inverse
+  // x transform (fork after MID, join before the next stencil)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int split_update = 1;
+  int upd_blocks = 1;
   std::vector<void*> allocs;
   size_t bytes = 0;
   double *cx = nullptr, *cy = nullptr, *cz = nullptr, *dg = nullptr, *stab = nullptr;
@@ -164,6 +170,9 @@ void free_plan(csl_plan* P) {
   if (P->graph) cudaGraphDestroy(P->graph);
   for (void* p : P->allocs) cudaFree(p);
   if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   delete P;
 }
 
@@ -416,13 +425,38 @@ RowArgs<T> p3_args(csl_plan* P, int par) {
   return r;
 }
 
+// the w/x update of the iteration with parity par (see k_update)
+template <typename T>
+cudaError_t launch_update(csl_plan* P, int par, cudaStream_t s) {
+  UpdateArgs u;
+  u.z = P->z[par];
+  u.wprev = P->w[par];
+  u.wcur = P->w[1 - par];
+  u.x = P->x;
+  u.st = P->st;
+  u.M = P->M;
+  k_update<typename C2<T>::t><<<P->upd_blocks, 256, 0, s>>>(u);
+  return cudaGetLastError();
+}
+
 // one MINRES iteration with buffer parity `par` (v_j in v[par], z_j in z[par])
 template <typename T>
 cudaError_t launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
   cudaError_t e = launch_stencil<T>(P, par, s, use_cond);
   if (e == cudaSuccess) e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, par), s);
   if (e == cudaSuccess) e = launch_mid_chain<T>(P, s, P->st, 2);
-  if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, par), s);
+  if (!P->split_update) {
+    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, par), s);
+    return e;
+  }
+  // fork: the update on the side stream, the inverse x transform (z_{j+1})
+  // on s; join before the next stencil, which reads both
+  if (e == cudaSuccess) e = cudaEventRecord(P->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->side, P->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_update<T>(P, par, P->side);
+  if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z, p3_args<T>(P, par), s);
+  if (e == cudaSuccess) e = cudaEventRecord(P->ev_join, P->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev_join, 0);
   return e;
 }
 
@@ -795,6 +829,9 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   nface[2] = dim == 3 ? (long)(nz + 1) * ny * nx : 0;
 
   cudaError_t err = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
   P->cx = (double*)dalloc(P, nface[0] * 8, &err);
   P->cy = (double*)dalloc(P, nface[1] * 8, &err);
   if (dim == 3) P->cz = (double*)dalloc(P, nface[2] * 8, &err);
@@ -834,6 +871,10 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   cudaStream_t s = P->stream;
   P->ew_blocks = (int)((M + 255) / 256 < kSMs * 8 ? (M + 255) / 256 : kSMs * 8);
+  {
+    const long chunks = (M + 256 * kUpdateUnroll - 1) / (256 * kUpdateUnroll);
+    P->upd_blocks = (int)(chunks < kSMs * 8 ? chunks : kSMs * 8);
+  }
 
   // coefficient faces: a_e / h^2, min / max / validity (Eq. 1 and Eq. 4's a_min, a_max)
   {
@@ -1217,11 +1258,14 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   const bool fp32 = P->precision != CSL_PREC_FP64;
-  const int nk = P->dim == 2 ? 4 : 6;
-  static const char* n2[4] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
-                              "k_row<LOAD_T,STORE_Z_UPDATE>"};
-  static const char* n3[6] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
-                              "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>"};
+  const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
+  const int nk = nkb + (P->split_update ? 1 : 0);
+  static const char* n2[5] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
+                              "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
+  static const char* n3[7] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
+                              "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
+  static const char* p3split = "k_row<LOAD_T,STORE_Z>";
+  const int st3 = P->split_update ? STORE_Z : STORE_Z_UPDATE;
   int k = 0;
   for (k = 0; k < nk && err == cudaSuccess; ++k) {
     double tot = 0.0;
@@ -1235,9 +1279,11 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
       } else if (k == 1) {
         err = fp32 ? run_row<float>(P, LOAD_LANCZOS, STORE_T, p1_args<float>(P, par), P->stream)
                    : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
-      } else if (k == nk - 1) {
-        err = fp32 ? run_row<float>(P, LOAD_T, STORE_Z_UPDATE, p3_args<float>(P, par), P->stream)
-                   : run_row<double>(P, LOAD_T, STORE_Z_UPDATE, p3_args<double>(P, par), P->stream);
+      } else if (k == nkb) {
+        err = fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
+      } else if (k == nkb - 1) {
+        err = fp32 ? run_row<float>(P, LOAD_T, st3, p3_args<float>(P, par), P->stream)
+                   : run_row<double>(P, LOAD_T, st3, p3_args<double>(P, par), P->stream);
       } else {
         const bool mid = (P->dim == 2) || (k == 3);
         const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
@@ -1267,7 +1313,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
       tot += t;
     }
     ms[k] = tot / reps;
-    names[k] = P->dim == 2 ? n2[k] : n3[k];
+    names[k] = (P->split_update && k == nkb - 1) ? p3split : P->dim == 2 ? n2[k] : n3[k];
   }
   P->st = keep;
   if (e0) cudaEventDestroy(e0);

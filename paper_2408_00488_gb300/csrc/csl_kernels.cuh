@@ -724,6 +724,58 @@ __device__ inline void givens_step(DevState* st, double g2) {
 // Ingest: f (complex128) -> b = [Im f; Re f] (block form, Eq. 2), MINRES
 // start vectors, ||b||, and the scalar state.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// MINRES direction and iterate update of iteration j as a streaming kernel
+// (run beside the inverse x transform of the same iteration, which does not
+// touch these vectors): w_{j+1} = ẑ_j + w_b w_{j-1} + w_c w_j (the w buffers
+// hold w scaled by its a1, so w_a = 1) over w_{j-1}'s buffer, and
+// x_j = x_{j-1} + x_coef w_{j+1}; the coefficients come from the Givens step
+// in the MID pass.  Per point: ẑ_j, w_{j-1}, w_j, x read, w_{j+1}, x written.
+// ---------------------------------------------------------------------------
+struct UpdateArgs {
+  const void* z;     // ẑ_j (TZ)
+  double2* wprev;    // in: w_{j-1}; out: w_{j+1}
+  const double2* wcur;
+  double2* x;
+  const DevState* st;
+  long M;
+};
+
+constexpr int kUpdateUnroll = 4;
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
+  if (a.st->done) return;
+  const double wb = a.st->w_b, wc = a.st->w_c, xc = a.st->x_coef;
+  const TZ* z = (const TZ*)a.z;
+  constexpr int U = kUpdateUnroll;
+  for (long c0 = (long)blockIdx.x * 256 * U; c0 < a.M; c0 += (long)gridDim.x * 256 * U) {
+    TZ zj[U];
+    double2 wp[U], wq[U], xo[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const long p = c0 + threadIdx.x + 256 * k;
+      if (p < a.M) {
+        zj[k] = z[p];
+        wp[k] = a.wprev[p];
+        wq[k] = a.wcur[p];
+        xo[k] = a.x[p];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const long p = c0 + threadIdx.x + 256 * k;
+      if (p < a.M) {
+        const double2 zd = to_d2(zj[k]);
+        const double2 wn = make_double2(fma(wb, wp[k].x, fma(wc, wq[k].x, zd.x)),
+                                        fma(wb, wp[k].y, fma(wc, wq[k].y, zd.y)));
+        a.wprev[p] = wn;
+        a.x[p] = make_double2(fma(xc, wn.x, xo[k].x), fma(xc, wn.y, xo[k].y));
+      }
+    }
+  }
+}
+
 struct IngestArgs {
   long M;
   const double2* f;
