@@ -741,7 +741,7 @@ struct UpdateArgs {
   long M;
 };
 
-constexpr int kUpdateUnroll = 4;
+constexpr int kUpdateUnroll = 2;
 
 template <typename TZ>
 __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
