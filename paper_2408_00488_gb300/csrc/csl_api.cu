@@ -725,8 +725,10 @@ csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status
     // prologue kernels + every launched WHILE body (two iterations each)
     const int per_iter = P->dim == 2 ? 4 : 6;
     const int prologue = 1 + per_iter;
+    const int it_launches = per_iter + (P->split_update ? 1 : 0);  // + k_update on the side branch
     const int bodies = (h.loops + 1) / 2;
-    info->launches = prologue + (P->graph_state == 1 ? bodies * 2 * per_iter : ((h.loops + 7) / 8) * 8 * per_iter);
+    info->launches =
+        prologue + (P->graph_state == 1 ? bodies * 2 * it_launches : ((h.loops + 7) / 8) * 8 * it_launches);
   }
   return CSL_OK;
 }
