@@ -485,10 +485,11 @@ cudaError_t launch_prologue_T(csl_plan* P, const double2* f, double tol, int max
   ia.maxit = maxit;
   ia.sqrt_pmin = P->sqrt_pmin;
   ia.sqrt_pmax = P->sqrt_pmax;
+  ia.vpair = sizeof(T) == 4 ? 1 : 0;
   k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   RowArgs<T> r1 = row_args<T>(P);
-  r1.vin = P->v[0];
+  r1.vin = P->b;  // v_1 = b (v[0] holds it as pairs in the FP32 forms)
   r1.tout = (typename C2<T>::t*)P->T;
   r1.st = P->st;
   if (e == cudaSuccess) e = run_row<T>(P, LOAD_V, STORE_T, r1, s);
@@ -1481,7 +1482,7 @@ cudaError_t build_group_args(csl_batch* B, BatchGroup& G) {
     yy.st = P->st;
     y[i] = yy;
     RowArgs<T> r1 = row_args<T>(P);
-    r1.vin = P->v[0];
+    r1.vin = P->b;  // v_1 = b
     r1.tout = (typename C2<T>::t*)P->T;
     r1.st = P->st;
     pro1[i] = r1;
@@ -1504,6 +1505,7 @@ cudaError_t build_group_args(csl_batch* B, BatchGroup& G) {
     ia.sqrt_pmin = P->sqrt_pmin;
     ia.sqrt_pmax = P->sqrt_pmax;
     ia.beta = P->beta;
+    ia.vpair = sizeof(T) == 4 ? 1 : 0;
     G.h_ing[i] = ia;
   }
   if (e == cudaSuccess) e = upload_array(B, &G.d_mid, mid);

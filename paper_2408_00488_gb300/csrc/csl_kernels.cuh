@@ -173,19 +173,45 @@ __device__ __forceinline__ void ff_acc_flux(ff2& acc, float2 c, float zc, float 
   ff_acc(acc, f.h, f.l);
 }
 
+// a * b for two pairs (the a.l * b.l term, below 2^-47 of the product, is dropped)
+__device__ __forceinline__ ff2 ff_mul(float2 a, float2 b) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pl = __fmaf_rn(a.x, b.x, -ph);
+  pl = __fmaf_rn(a.x, b.y, pl);
+  pl = __fmaf_rn(a.y, b.x, pl);
+  return {ph, pl};
+}
+
 __device__ __forceinline__ double ff_to_d(ff2 v) { return f2d_exact(v.h) + f2d_exact(v.l); }
 
-// float -> double by field moves without branches, for the halves of a pair
-// on their way into an FP64 vector: normal floats, zeros, infinities and NaN
-// convert exactly; a subnormal float (|f| < 2^-126) becomes a signed zero.
-__device__ __forceinline__ double f2d_ftz(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned ex = e == 255u ? 0x7ffu : e + 896u;
-  const unsigned hi = (u & 0x80000000u) | (ex << 20) | ((u >> 3) & 0xfffffu);
-  const bool z = e == 0u;
-  return __hiloint2double((int)(z ? (u & 0x80000000u) : hi), (int)(z ? 0u : (u << 29)));
+// a double as a float pair hi + lo, hi = RN(d), lo = RN(d - hi) (d - hi is exact)
+__device__ __forceinline__ float2 d_to_ff(double d) {
+  const float h = d2f_rn(d);
+  return make_float2(h, d2f_rn(d - f2d_exact(h)));
 }
+
+// Lanczos vectors v (and u'): FP64 in the FP64 form; in the FP32 forms each
+// component is a float pair (re.hi, re.lo, im.hi, im.lo) in the same 16 bytes
+// per point, so that the stencil and the Lanczos step run in pair arithmetic.
+template <typename TZ>
+__device__ __forceinline__ double2 v_load(const double2* v, long p) {
+  if constexpr (sizeof(TZ) == 16) {
+    return v[p];
+  } else {
+    const float4 q = ((const float4*)v)[p];
+    return make_double2(f2d_exact(q.x) + f2d_exact(q.y), f2d_exact(q.z) + f2d_exact(q.w));
+  }
+}
+template <typename TZ>
+__device__ __forceinline__ void v_store(double2* v, long p, double2 val) {
+  if constexpr (sizeof(TZ) == 16) {
+    v[p] = val;
+  } else {
+    const float2 a = d_to_ff(val.x), b = d_to_ff(val.y);
+    ((float4*)v)[p] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 
 __device__ __forceinline__ float2 shfl_up_f2(float2 v) {
   return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
@@ -330,7 +356,7 @@ struct StepOperands {
       ce = a.cx[rx + 1];
       cs = a.cy[ry];
       cn = a.cy[ry + nx];
-      vo = a.vold[p];
+      vo = v_load<TZ>(a.vold, p);
     }
   }
 };
@@ -387,7 +413,7 @@ __host__ __device__ constexpr int ff_stencil_smem(int dim) {
 // beta block term and delta in pairs, and leave 4 FP64 operations per point
 // (u' = A ẑ - lanc v_{j-1} against the FP64 Lanczos vector).
 template <int DIM, typename TZ, bool FF>
-__global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
+__global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
   static_assert(!FF || sizeof(TZ) == 8, "the float-pair stencil reads an FP32 z");
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
   const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
@@ -414,10 +440,10 @@ __global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, con
   const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz, strip);
   double acc[2] = {0.0, 0.0};
   ff2 dacc = {0.f, 0.f};
-  float2 beta2 = make_float2(0.f, 0.f);
+  float2 beta2 = make_float2(0.f, 0.f), lanc2 = make_float2(0.f, 0.f);
   if (FF) {
-    const float bh = d2f_rn(beta);
-    beta2 = make_float2(bh, d2f_rn(beta - f2d_exact(bh)));
+    beta2 = d_to_ff(beta);
+    lanc2 = d_to_ff(lanc);
   }
   for (long s = (long)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
        s += (long)nblk * (blockDim.x >> 5)) {
@@ -523,9 +549,12 @@ __global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, con
           ff_acc_mul1(kx, nbeta2, zc.y);
           ff_acc_mul1(dacc, make_float2(ky.h, ky.l), zc.x);
           ff_acc_mul1(dacc, make_float2(kx.h, kx.l), zc.y);
-          const double2 vo = S.v[lane];
-          a.vold[p] = make_double2(fma(-lanc, vo.x, f2d_ftz(ky.h)) + f2d_ftz(ky.l),
-                                   fma(-lanc, vo.y, f2d_ftz(kx.h)) + f2d_ftz(kx.l));
+          // u' = A z - lanc v_{j-1}, all in pairs (v_{j-1} is stored as pairs)
+          const float4 vo = *(const float4*)&S.v[lane];
+          const ff2 px = ff_mul(lanc2, make_float2(vo.x, vo.y)), py = ff_mul(lanc2, make_float2(vo.z, vo.w));
+          ff_acc(ky, -px.h, -px.l);
+          ff_acc(kx, -py.h, -py.l);
+          ((float4*)a.vold)[p] = make_float4(ky.h, ky.l, kx.h, kx.l);
         }
         __syncwarp();  // every lane is done with this slot before it is refilled
         zm = zc;
@@ -574,7 +603,7 @@ __global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, con
           }
           const double2 Az = block_A(make_double2(ax, ay), zc, beta);
           acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
-          a.vold[p] = make_double2(fma(-lanc, cur.vo.x, Az.x), fma(-lanc, cur.vo.y, Az.y));
+          v_store<TZ>(a.vold, p, make_double2(fma(-lanc, cur.vo.x, Az.x), fma(-lanc, cur.vo.y, Az.y)));
         }
         zm = zc;
         zc = zp;
@@ -595,8 +624,8 @@ __global__ void __launch_bounds__(256, FF ? 3 : 1) k_stencil(StencilArgs a0, con
         const double2 zc = wz.zc;
         const double2 Az = block_A(t, zc, beta);
         acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
-        const double2 vo = a.vold[p];
-        a.vold[p] = make_double2(fma(-lanc, vo.x, Az.x), fma(-lanc, vo.y, Az.y));
+        const double2 vo = v_load<TZ>(a.vold, p);
+        v_store<TZ>(a.vold, p, make_double2(fma(-lanc, vo.x, Az.x), fma(-lanc, vo.y, Az.y)));
         if (check) {
           const double2 Ax = block_A(tx, wx.zc, beta);
           const double2 bb = a.b[p];
@@ -784,6 +813,7 @@ struct IngestArgs {
   double* partials;
   double tol, beta, sqrt_pmin, sqrt_pmax;
   int maxit;
+  int vpair;  // FP32 forms: v stored as float pairs
 };
 
 static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const IngestArgs* batch, int bps) {
@@ -797,7 +827,12 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const Inge
     const double2 fv = a.f[p];
     const double2 bb = make_double2(fv.y, fv.x);
     a.b[p] = bb;
-    a.v0[p] = bb;
+    if (a.vpair) {  // FP32 forms: v as float pairs (see v_store)
+      const float2 re = d_to_ff(bb.x), im = d_to_ff(bb.y);
+      ((float4*)a.v0)[p] = make_float4(re.x, re.y, im.x, im.y);
+    } else {
+      a.v0[p] = bb;
+    }
     a.v1[p] = zero;
     a.w0[p] = zero;
     a.w1[p] = zero;

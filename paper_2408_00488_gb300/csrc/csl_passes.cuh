@@ -152,7 +152,40 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     // global loads in batches of UB elements per lane, all issued before use
 #pragma unroll
     for (int i0 = 0; i0 < NL; i0 += UB) {
-      if (LOAD == LOAD_LANCZOS) {
+      if (LOAD == LOAD_LANCZOS && sizeof(T) == 4) {
+        // FP32 forms: u' and v_j are float pairs (re.hi, re.lo, im.hi, im.lo);
+        // v_{j+1} = u' - (delta/gamma) v_j in pair arithmetic, stored
+        // renormalised, its hi parts (= RN of the pair) feed the transform
+        float4 u[UB], vc[UB];
+        const float2 lz2 = d_to_ff(lz);
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          if (valid && j < n) {
+            u[k] = ((const float4*)a.vnew)[base + j];
+            vc[k] = ((const float4*)a.vcur)[base + j];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          const int j = t + TPL * (i0 + k);
+          if (j < n) {
+            c_t val = mkc<T>((T)0, (T)0);
+            if (valid) {
+              ff2 rx = {u[k].x, u[k].y}, ry = {u[k].z, u[k].w};
+              const ff2 px = ff_mul(lz2, make_float2(vc[k].x, vc[k].y));
+              const ff2 py = ff_mul(lz2, make_float2(vc[k].z, vc[k].w));
+              ff_acc(rx, -px.h, -px.l);
+              ff_acc(ry, -py.h, -py.l);
+              rx = ff_two_sum(rx.h, rx.l);
+              ry = ff_two_sum(ry.h, ry.l);
+              ((float4*)a.vnew)[base + j] = make_float4(rx.h, rx.l, ry.h, ry.l);
+              val = mkc<T>((T)rx.h, (T)ry.h);
+            }
+            line[D::in_pos(j + 1)] = val;
+          }
+        }
+      } else if (LOAD == LOAD_LANCZOS) {
         double2 u[UB], vc[UB];
 #pragma unroll
         for (int k = 0; k < UB; ++k) {
