@@ -734,6 +734,13 @@ csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status
   return CSL_OK;
 }
 
+// the iterate x to the caller's FP64 vector (the FP32 forms hold it as float pairs)
+cudaError_t copy_out(csl_plan* P, double2* dst, cudaStream_t s) {
+  if (P->precision == CSL_PREC_FP64) return cudaMemcpyAsync(dst, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, s);
+  k_x_out<<<P->ew_blocks, 256, 0, s>>>((const float4*)P->x, dst, P->M);
+  return cudaGetLastError();
+}
+
 csl_status solve_impl(csl_plan* P, const double2* f, double tol, int maxit, double beta) {
   if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
   CSL_TRY(launch_prologue(P, f, tol, maxit, beta, P->stream));
@@ -1194,7 +1201,7 @@ csl_status csl_solve(csl_plan* P, const double* f, double* z, double tol, int ma
   if (!P || !f || !z) return CSL_INVALID_ARG;
   csl_status s = solve_impl(P, (const double2*)f, tol, maxit, P->beta);
   if (s != CSL_OK) return s;
-  CSL_TRY(cudaMemcpyAsync(z, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  CSL_TRY(copy_out(P, (double2*)z, P->stream));
   csl_status st = CSL_OK;
   s = read_info(P, info, &st);
   return s != CSL_OK ? s : st;
@@ -1204,7 +1211,7 @@ csl_status csl_adjoint(csl_plan* P, const double* g, double* y, double tol, int 
   if (!P || !g || !y) return CSL_INVALID_ARG;
   csl_status s = solve_impl(P, (const double2*)g, tol, maxit, -P->beta);
   if (s != CSL_OK) return s;
-  CSL_TRY(cudaMemcpyAsync(y, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  CSL_TRY(copy_out(P, (double2*)y, P->stream));
   csl_status st = CSL_OK;
   s = read_info(P, info, &st);
   return s != CSL_OK ? s : st;
@@ -1218,7 +1225,8 @@ csl_status csl_solve_host(csl_plan* P, const double* f_host, double* z_host, dou
   CSL_TRY(cudaMemcpyAsync(P->io, f_host, bytes, cudaMemcpyHostToDevice, P->stream));
   csl_status s = solve_impl(P, P->io, tol, maxit, P->beta);
   if (s != CSL_OK) return s;
-  CSL_TRY(cudaMemcpyAsync(z_host, P->x, bytes, cudaMemcpyDeviceToHost, P->stream));
+  CSL_TRY(copy_out(P, P->io, P->stream));  // f is no longer needed
+  CSL_TRY(cudaMemcpyAsync(z_host, P->io, bytes, cudaMemcpyDeviceToHost, P->stream));
   csl_status st = CSL_OK;
   s = read_info(P, info, &st);
   return s != CSL_OK ? s : st;
@@ -1378,12 +1386,14 @@ __global__ void k_batch_control(DevState* states, int nsys, int* loops, cudaGrap
   }
 }
 
-__global__ void k_batch_copy(const double2* const* src, double2* const* dst, const long* count) {
+// egress of a batch: x of every system to its z (pairs = FP32 forms, x held as float pairs)
+__global__ void k_batch_copy(const double2* const* src, double2* const* dst, const long* count, int pairs) {
   const int s = blockIdx.y;
   const double2* a = src[s];
   double2* b = dst[s];
   const long M = count[s];
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (long)gridDim.x * blockDim.x) b[i] = a[i];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (long)gridDim.x * blockDim.x)
+    b[i] = pairs ? to_d2(((const float4*)a)[i]) : a[i];
 }
 
 }  // namespace
@@ -1669,7 +1679,7 @@ csl_status batch_solve_T(csl_batch* B, const double* const* f, double* const* z,
   CSL_TRY(cudaMemcpyAsync(B->d_dst, dst.data(), sizeof(void*) * B->nsys, cudaMemcpyHostToDevice, s));
   CSL_TRY(cudaMemcpyAsync(B->d_count, cnt.data(), sizeof(long) * B->nsys, cudaMemcpyHostToDevice, s));
   dim3 grid((unsigned)((B->maxM + 255) / 256 < 256 ? (B->maxM + 255) / 256 : 256), (unsigned)B->nsys);
-  k_batch_copy<<<grid, 256, 0, s>>>(B->d_src, B->d_dst, B->d_count);
+  k_batch_copy<<<grid, 256, 0, s>>>(B->d_src, B->d_dst, B->d_count, sizeof(T) == 4 ? 1 : 0);
   CSL_TRY(cudaGetLastError());
   std::vector<DevState> h(B->nsys);
   CSL_TRY(cudaMemcpyAsync(h.data(), B->states, sizeof(DevState) * B->nsys, cudaMemcpyDeviceToHost, s));

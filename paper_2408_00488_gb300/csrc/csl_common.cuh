@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace csl {
 
 template <typename T> struct C2;
@@ -58,6 +60,11 @@ __device__ __forceinline__ float d2f_rn(double d) {
 
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(f2d_exact(v.x), f2d_exact(v.y)); }
+// a complex value held as two float pairs (re.hi, re.lo, im.hi, im.lo): the
+// FP32 forms' storage of the MINRES vectors v, w and x
+__device__ __forceinline__ double2 to_d2(float4 v) {
+  return make_double2(f2d_exact(v.x) + f2d_exact(v.y), f2d_exact(v.z) + f2d_exact(v.w));
+}
 template <typename T> __device__ __forceinline__ typename C2<T>::t from_d2(double2 v);
 template <> __device__ __forceinline__ double2 from_d2<double>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 from_d2<float>(double2 v) {

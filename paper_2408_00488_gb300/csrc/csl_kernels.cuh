@@ -611,15 +611,18 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
       }
       continue;
     }
+    // x is FP64 in the FP64 form and float pairs in the FP32 forms
+    typedef typename std::conditional<sizeof(TZ) == 8, float4, double2>::type TX;
+    const TX* xs = (const TX*)a.x;
     StripWindow<DIM, TZ> wz;
-    StripWindow<DIM, double2> wx;
+    StripWindow<DIM, TX> wx;
     wz.start(z, base, mstride, m0, vx);
-    wx.start(a.x, base, mstride, m0, vx);
+    wx.start(xs, base, mstride, m0, vx);
     for (int m = m0; m < m1; ++m) {
       const long p = base + (long)m * mstride;
       const double2 t = wz.KA(z, a, p, mstride, m, nm, x, yfix, vx, lane);
       double2 tx = make_double2(0.0, 0.0);
-      if (check) tx = wx.KA(a.x, a, p, mstride, m, nm, x, yfix, vx, lane);
+      if (check) tx = wx.KA(xs, a, p, mstride, m, nm, x, yfix, vx, lane);
       if (vx) {
         const double2 zc = wz.zc;
         const double2 Az = block_A(t, zc, beta);
@@ -772,37 +775,92 @@ struct UpdateArgs {
 
 constexpr int kUpdateUnroll = 2;
 
+// one component of the pair update: w_{j+1} = z + wb w_{j-1} + wc w_j and
+// x_j = x_{j-1} + xc w_{j+1}, all float pairs (renormalised on store)
+__device__ __forceinline__ void ff_update(float z, float2 wp, float2 wq, float2 xo, float2 wb2, float2 wc2,
+                                          float2 xc2, ff2& wn, ff2& xn) {
+  ff2 acc = {z, 0.f};
+  const ff2 p1 = ff_mul(wc2, wq), p2 = ff_mul(wb2, wp);
+  ff_acc(acc, p1.h, p1.l);
+  ff_acc(acc, p2.h, p2.l);
+  wn = ff_two_sum(acc.h, acc.l);
+  const ff2 p3 = ff_mul(xc2, make_float2(wn.h, wn.l));
+  ff2 xa = {xo.x, xo.y};
+  ff_acc(xa, p3.h, p3.l);
+  xn = ff_two_sum(xa.h, xa.l);
+}
+
 template <typename TZ>
 __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
   if (a.st->done) return;
   const double wb = a.st->w_b, wc = a.st->w_c, xc = a.st->x_coef;
   const TZ* z = (const TZ*)a.z;
   constexpr int U = kUpdateUnroll;
-  for (long c0 = (long)blockIdx.x * 256 * U; c0 < a.M; c0 += (long)gridDim.x * 256 * U) {
-    TZ zj[U];
-    double2 wp[U], wq[U], xo[U];
+  if constexpr (sizeof(TZ) == 8) {  // FP32 forms: w and x as float pairs
+    const float2 wb2 = d_to_ff(wb), wc2 = d_to_ff(wc), xc2 = d_to_ff(xc);
+    const float4* wq4 = (const float4*)a.wcur;
+    float4* wp4 = (float4*)a.wprev;
+    float4* x4 = (float4*)a.x;
+    for (long c0 = (long)blockIdx.x * 256 * U; c0 < a.M; c0 += (long)gridDim.x * 256 * U) {
+      float2 zj[U];
+      float4 wp[U], wq[U], xo[U];
 #pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long p = c0 + threadIdx.x + 256 * k;
-      if (p < a.M) {
-        zj[k] = z[p];
-        wp[k] = a.wprev[p];
-        wq[k] = a.wcur[p];
-        xo[k] = a.x[p];
+      for (int k = 0; k < U; ++k) {
+        const long p = c0 + threadIdx.x + 256 * k;
+        if (p < a.M) {
+          zj[k] = ((const float2*)z)[p];
+          wp[k] = wp4[p];
+          wq[k] = wq4[p];
+          xo[k] = x4[p];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const long p = c0 + threadIdx.x + 256 * k;
+        if (p < a.M) {
+          ff2 wr, xr, wi, xi;
+          ff_update(zj[k].x, make_float2(wp[k].x, wp[k].y), make_float2(wq[k].x, wq[k].y),
+                    make_float2(xo[k].x, xo[k].y), wb2, wc2, xc2, wr, xr);
+          ff_update(zj[k].y, make_float2(wp[k].z, wp[k].w), make_float2(wq[k].z, wq[k].w),
+                    make_float2(xo[k].z, xo[k].w), wb2, wc2, xc2, wi, xi);
+          wp4[p] = make_float4(wr.h, wr.l, wi.h, wi.l);
+          x4[p] = make_float4(xr.h, xr.l, xi.h, xi.l);
+        }
       }
     }
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long p = c0 + threadIdx.x + 256 * k;
-      if (p < a.M) {
-        const double2 zd = to_d2(zj[k]);
-        const double2 wn = make_double2(fma(wb, wp[k].x, fma(wc, wq[k].x, zd.x)),
-                                        fma(wb, wp[k].y, fma(wc, wq[k].y, zd.y)));
-        a.wprev[p] = wn;
-        a.x[p] = make_double2(fma(xc, wn.x, xo[k].x), fma(xc, wn.y, xo[k].y));
+  } else {
+    for (long c0 = (long)blockIdx.x * 256 * U; c0 < a.M; c0 += (long)gridDim.x * 256 * U) {
+      TZ zj[U];
+      double2 wp[U], wq[U], xo[U];
+  #pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const long p = c0 + threadIdx.x + 256 * k;
+        if (p < a.M) {
+          zj[k] = z[p];
+          wp[k] = a.wprev[p];
+          wq[k] = a.wcur[p];
+          xo[k] = a.x[p];
+        }
+      }
+  #pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const long p = c0 + threadIdx.x + 256 * k;
+        if (p < a.M) {
+          const double2 zd = to_d2(zj[k]);
+          const double2 wn = make_double2(fma(wb, wp[k].x, fma(wc, wq[k].x, zd.x)),
+                                          fma(wb, wp[k].y, fma(wc, wq[k].y, zd.y)));
+          a.wprev[p] = wn;
+          a.x[p] = make_double2(fma(xc, wn.x, xo[k].x), fma(xc, wn.y, xo[k].y));
+        }
       }
     }
   }
+}
+
+// the FP32 forms' iterate (float pairs) as FP64 values for the caller
+static __global__ void k_x_out(const float4* __restrict__ x, double2* __restrict__ out, long M) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (long)gridDim.x * blockDim.x)
+    out[p] = to_d2(x[p]);
 }
 
 struct IngestArgs {

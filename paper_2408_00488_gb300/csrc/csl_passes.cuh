@@ -135,10 +135,16 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   // known once the MID pass has run, so the z store applies it
   T zs = (T)1;
   if ((STORE == STORE_Z || STORE == STORE_Z_UPDATE) && a.st) zs = (T)(a.st->gam > 0.0 ? 1.0 / a.st->gam : 0.0);
+  float2 wb2 = make_float2(0.f, 0.f), wc2 = wb2, xc2 = wb2;
   if (STORE == STORE_Z_UPDATE) {
     wb = a.st->w_b;
     wc = a.st->w_c;
     xc = a.st->x_coef;
+    if (sizeof(T) == 4) {
+      wb2 = d_to_ff(wb);
+      wc2 = d_to_ff(wc);
+      xc2 = d_to_ff(xc);
+    }
   }
   __syncthreads();
   const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
@@ -248,6 +254,17 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
               const long p = base + j;
               const c_t F = line[D::out_pos(j + 1)];
               a.zout[p] = mkc<T>(F.x * zs, F.y * zs);
+              if constexpr (sizeof(T) == 4) {  // FP32 forms: w and x as float pairs (see k_update)
+                const float4 q = *(const float4*)&wp[k], r = *(const float4*)&wq[k], o = *(const float4*)&xo[k];
+                ff2 wr, xr, wi, xi;
+                ff_update(zo[k].x, make_float2(q.x, q.y), make_float2(r.x, r.y), make_float2(o.x, o.y), wb2, wc2, xc2,
+                          wr, xr);
+                ff_update(zo[k].y, make_float2(q.z, q.w), make_float2(r.z, r.w), make_float2(o.z, o.w), wb2, wc2, xc2,
+                          wi, xi);
+                ((float4*)a.wprev)[p] = make_float4(wr.h, wr.l, wi.h, wi.l);
+                ((float4*)a.x)[p] = make_float4(xr.h, xr.l, xi.h, xi.l);
+                continue;
+              }
               const double2 zd = to_d2(zo[k]);
               // scaled w: w_a = 1 (see givens_step)
               const double2 wn = make_double2(fma(wb, wp[k].x, fma(wc, wq[k].x, zd.x)),
