@@ -159,18 +159,16 @@ def kernel_model(name, M, d, prec, N, ff=False):
     f64 = f32 = 0.0
     if name == "k_stencil" and ff:
         b = sT + 16 + 16 + 8 * d
-        f64 = 6                 # u' = A z - lanc v: one FMA and one add per component
-        f32 = 2 * (50 + 72 * d)  # pair arithmetic: alpha, 2d fluxes, beta and delta terms, 2 components
+        f32 = 2 * (74 + 72 * d)  # pair arithmetic: alpha, 2d fluxes, beta, delta and u' terms, 2 components
     elif name == "k_stencil":
         b = sT + 16 + 16 + 8 + 8 * d
         f64 = 16 + 8 * d
     elif name.startswith("k_row<LOAD_LANCZOS"):
         b = 16 + 16 + 16 + sT
-        f64 = 4
         if prec == "fp64":
-            f64 += dst_flops
+            f64 = 4 + dst_flops
         else:
-            f32 += dst_flops
+            f32 = 2 * 36 + dst_flops  # the Lanczos step in float pairs
     elif name.startswith("k_row<LOAD_T,STORE_Z_UPDATE"):
         b = sT + sT + 48 + sT + 32
         f64 = 14
@@ -186,7 +184,10 @@ def kernel_model(name, M, d, prec, N, ff=False):
             f32 += dst_flops
     elif name == "k_update":  # w_{j+1}, x_j: z_j, w_{j-1}, w_j, x in; w_{j+1}, x out
         b = sT + 80
-        f64 = 12
+        if prec == "fp64":
+            f64 = 12
+        else:
+            f32 = 2 * 96  # float pairs
     elif name == "k_strided<mid>":
         b = 2 * sT + (8 if prec == "fp64" else 0)
         fl = 2 * dst_flops + 7
