@@ -394,20 +394,39 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
         T murest = a.mu_col ? a.mu_col[ix] : (T)0;
         if (a.mu_outer) murest += a.mu_outer[o];
         T part = (T)0;
-        for (int m = 1 + t; m <= n; m += TPL) {
-          const int pos = D::out_pos(m);
-          c_t F = line[pos];
-          T sc;
-          if (a.stab) {
-            sc = (T)a.stab[base + (long)(m - 1) * a.line_stride + myl];
-          } else {
-            const T e = fma(a.gamma, murest + a.mu_line[m - 1], a.alpha);
-            sc = a.cnorm * rsq(fma(e, e, a.beta2));
+        if (a.stab) {
+          for (int m = 1 + t; m <= n; m += TPL) {
+            const int pos = D::out_pos(m);
+            c_t F = line[pos];
+            const T sc = (T)a.stab[base + (long)(m - 1) * a.line_stride + myl];
+            part = fma(sc, fma(F.x, F.x, F.y * F.y), part);
+            F.x *= sc;
+            F.y *= sc;
+            line[pos] = F;
           }
-          part = fma(sc, fma(F.x, F.x, F.y * F.y), part);
-          F.x *= sc;
-          F.y *= sc;
-          line[pos] = F;
+        } else {
+          // the lane's eigenvalues mu_m are loaded together before the
+          // scaling, so their latencies overlap instead of adding up
+          T mu[NL];
+#pragma unroll
+          for (int k = 0; k < NL; ++k) {
+            const int m = 1 + t + TPL * k;
+            mu[k] = m <= n ? a.mu_line[m - 1] : (T)0;
+          }
+#pragma unroll
+          for (int k = 0; k < NL; ++k) {
+            const int m = 1 + t + TPL * k;
+            if (m <= n) {
+              const int pos = D::out_pos(m);
+              c_t F = line[pos];
+              const T e = fma(a.gamma, murest + mu[k], a.alpha);
+              const T sc = a.cnorm * rsq(fma(e, e, a.beta2));
+              part = fma(sc, fma(F.x, F.x, F.y * F.y), part);
+              F.x *= sc;
+              F.y *= sc;
+              line[pos] = F;
+            }
+          }
         }
         g2acc += (double)part;
       }
