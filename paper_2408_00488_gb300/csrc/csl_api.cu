@@ -523,8 +523,9 @@ cudaError_t launch_precondition_T(csl_plan* P, const double2* v, double2* out, c
 
 // ---- autotuner ---------------------------------------------------------------
 // Each sine-transform pass is timed (CUDA events on the plan's stream, the
-// plan's own buffers, a scratch solver state) for every CTA size and, for
-// N = 512 and 1024, both transform variants; the fastest is kept.  Results are
+// plan's own buffers, a scratch solver state; the fastest of 5 launches) for
+// every CTA size and, for N = 512 and 1024, every transform variant; the
+// fastest candidate is kept.  Results are
 // cached per (precision, pass, geometry) for the life of the process.
 struct TuneKey {
   int prec, kind, N, ncols, nouter;
@@ -547,7 +548,9 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
     const PassCfg keep = P->row;
     P->row = c;
     cudaError_t e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, 0), P->stream);
-    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, 0), P->stream);
+    // P3 as the solve runs it (the update on its own branch, or fused)
+    if (e == cudaSuccess)
+      e = run_row<T>(P, LOAD_T, P->split_update ? STORE_Z : STORE_Z_UPDATE, p3_args<T>(P, 0), P->stream);
     P->row = keep;
     return e;
   }
@@ -555,7 +558,9 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
   a.st = P->st;
   if (kind == 2) {
     fill_mid<T>(P, a, axis);
-    a.scalar_mode = 2;
+    // no Givens tail while tuning: on the zero tuning data it would end the
+    // scratch solve, and the next launch of a timed group would return at once
+    a.scalar_mode = 0;
   }
   return launch_strided<T>(c.N, c.wide, kind == 2, a, c.L, P->stream);
 }
@@ -594,17 +599,20 @@ cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e
         tiles = (long)((c.ncols + lines - 1) / lines) * c.nouter;
         cand.L.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
       }
-      float tot = 0.f;
+      // the fastest of 5 timed groups (after one warm-up) of 3 back-to-back
+      // launches: the host's submission hides behind the GPU's execution, and
+      // a group delayed by something else on the GPU is discarded
+      float tot = 1e30f;
       cudaError_t e = cudaSuccess;
-      for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+      for (int r = 0; r < 6 && e == cudaSuccess; ++r) {
         e = cudaMemcpyAsync(P->st, &hst, sizeof(hst), cudaMemcpyHostToDevice, P->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
-        if (e == cudaSuccess) e = tune_launch<T>(P, kind, cand, axis);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = tune_launch<T>(P, kind, cand, axis);
         if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float t = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-        if (r > 0) tot += t;  // the first launch warms up
+        if (r > 0 && t < tot) tot = t;
       }
       if (e != cudaSuccess) return e;
       if (tot < best_ms) {
