@@ -65,8 +65,11 @@ typedef enum csl_status {
 
 typedef enum csl_precision {
   CSL_PREC_FP64 = 0,  /* every step in FP64 (the plain method)                          */
-  CSL_PREC_FP32 = 1,  /* sine transforms and per-mode scale of P^{-1} in FP32; stencil,
-                         Lanczos recurrence, Givens rotations and residual norms in FP64 */
+  CSL_PREC_FP32 = 1,  /* sine transforms and per-mode scale of P^{-1} in FP32; the
+                         per-point vector work (stencil, Lanczos step, w/x update) in
+                         float-pair arithmetic (about 2^-47 relative); Lanczos and Givens
+                         scalars, reductions and the true-residual check in FP64; the
+                         solution is returned in FP64 */
   CSL_PREC_BF16X3 = 2, /* as CSL_PREC_FP32, but the transforms along y and z (lines of
                           n+1 = 32, 64 or 128 points) run on the tensor cores as GEMMs with
                           the sine matrix of Section 2.3: operands split into two bf16 terms,

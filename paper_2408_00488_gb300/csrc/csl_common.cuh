@@ -84,7 +84,7 @@ struct DevState {
   double gam, gam_old, gam1, delta;
   // Givens rotations (c_j, c_{j-1}, s_j, s_{j-1}) and the rotated right-hand side eta
   double c, c_old, s, s_old, eta;
-  // coefficients of the fused update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1};
+  // coefficients of the update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1};
   // the w vectors are kept scaled by the a1 of the step that made them
   // (w_a = 1), a1_old / a1_old2 being those of the last two steps
   double w_a, w_b, w_c, x_coef, a1_old, a1_old2;

@@ -1,6 +1,6 @@
 // Kernels of the preconditioned MINRES solve of Eq. 2 with the preconditioner
 // of Eq. 4 (arXiv 2408.00488).  One MINRES iteration j is four (2D) or six
-// (3D) stream-ordered kernels:
+// (3D) stream-ordered kernels plus the update on a parallel branch:
 //
 //   S   k_stencil     u' = A z_j / gamma_j - (gamma_j/gamma_{j-1}) v_{j-1}     (Eq. 2)
 //                     delta_j = <A zhat_j, zhat_j>;  optionally the true residual
@@ -11,8 +11,12 @@
 //                     gamma_{j+1}^2 = sum_k s_k |v^_k|^2 (Parseval), inverse DST;
 //                     last block: Givens rotation and update coefficients
 //   (3D: k_strided along y)
-//   P3  k_row<STORE_Z_UPDATE> inverse DST along x -> z_{j+1};
-//                     w_{j+1} = (zhat_j - a3 w_{j-1} - a2 w_j)/a1,  x_j = x_{j-1} + c eta w_{j+1}
+//   P3  k_row<STORE_Z> inverse DST along x -> z_{j+1}, and beside it
+//   UPD k_update       w_{j+1} = (zhat_j - a3 w_{j-1} - a2 w_j)/a1,  x_j = x_{j-1} + c eta w_{j+1}
+//                     (batches fuse UPD into P3: k_row<STORE_Z_UPDATE>)
+//
+// The FP32 forms hold v, w and x as float pairs and run the per-point vector
+// work in pair arithmetic; the FP64 form holds them in FP64.
 //
 // The grid reductions are deterministic (block sums in block order by the
 // last block to finish), so repeated solves are bitwise identical.

@@ -1,5 +1,6 @@
-// Sine-transform passes of P^{-1} (Eq. 4 via Section 2.3) with the MINRES
-// vector work fused into the first and last pass.
+// Sine-transform passes of P^{-1} (Eq. 4 via Section 2.3) with MINRES vector
+// work fused into the first pass (the Lanczos step) and, for batches, into
+// the last one (the w/x update; single solves run it beside that pass).
 //
 //   k_row     DST along x (contiguous rows).  Each warp owns 32/TPL rows: it
 //             loads them (fusing v_{j+1} = u' - (delta_j/gamma_j) v_j when
