@@ -618,7 +618,7 @@ def main():
         line = {
             "metric": METRIC, "value": job_rate(1, world, ms_mixed), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 inside P^-1)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (float-pair vectors; f64 scalars and residual check; f32 inside P^-1)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32-preconditioner MINRES (FP64 stencil/Lanczos/Givens)",
                        "l2": "flushed (256 MiB write) before every step", "parallelism": "replicas" if world > 1
                        else "single GPU"},
