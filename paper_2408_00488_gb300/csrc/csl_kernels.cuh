@@ -100,7 +100,7 @@ __device__ __forceinline__ void point_coords(long p, const Grid& g, int& ix, int
 struct StencilArgs {
   Grid g;
   const void* z;          // z_j (unnormalised), TZ
-  double2* vold;          // in: v_{j-1}; out: u'
+  double2* vold;          // in: v_{j-1}; out: u' (FP64, or float pairs in the FP32 forms)
   const double* cx;
   const double* cy;
   const double* cz;
@@ -413,9 +413,9 @@ __host__ __device__ constexpr int ff_stencil_smem(int dim) {
 // FF (FP32 ẑ only): the non-checking steps form (K + alpha I) ẑ in the
 // difference form alpha z_p + sum_e c_e (z_p - z_q) of Eq. 1 in float-pair
 // arithmetic (the differences of neighbouring values are exact and small, so
-// the large cancelling terms c_e z_p of the direct form never appear), add the
-// beta block term and delta in pairs, and leave 4 FP64 operations per point
-// (u' = A ẑ - lanc v_{j-1} against the FP64 Lanczos vector).
+// the large cancelling terms c_e z_p of the direct form never appear), and
+// add the beta block term, delta and u' = A ẑ - lanc v_{j-1} (v held as float
+// pairs) in pairs too: no FP64 arithmetic per point.
 template <int DIM, typename TZ, bool FF>
 __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
   static_assert(!FF || sizeof(TZ) == 8, "the float-pair stencil reads an FP32 z");

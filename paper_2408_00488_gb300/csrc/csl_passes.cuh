@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   const RowArgs<T> a = batch ? batch[sys] : a0;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
-  // load batch: the Lanczos and update variants keep 2 and 4 FP64 vectors per
-  // element in flight, so they batch fewer elements (128-register FP32 budget)
+  // load batch: the Lanczos and update variants keep 2 and 4 16-byte vector
+  // values (FP64, or float pairs) per element in flight, so they batch fewer
+  // elements (128-register FP32 budget)
   constexpr int UBMAX = STORE == STORE_Z_UPDATE ? 2 : LOAD == LOAD_LANCZOS ? 4 : 8;
   constexpr int UB = NL < UBMAX ? NL : UBMAX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
