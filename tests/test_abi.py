@@ -85,3 +85,52 @@ def test_host_side_argument_validation(csl):
     assert csl.lib.csl_plan_workspace_bytes(None) == 0
     assert csl.lib.csl_plan_config(None) == b""
     csl.lib.csl_plan_destroy(None)
+
+
+C_TYPES = {"int": ctypes.c_int, "double": ctypes.c_double, "int64_t": ctypes.c_int64,
+           "const double*": ctypes.c_void_p, "double*": ctypes.c_void_p, "void*": ctypes.c_void_p}
+
+
+def header_struct(name):
+    """(field name, ctypes type, array length) of `typedef struct name {...} name;` in csl.h."""
+    text = open(os.path.join(ROOT, "include", "csl.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(const\s+)?(\w+)\s*(\*?)\s*(.*)$", decl)
+        assert m, decl
+        ctype = ((m.group(1) or "") + m.group(2) + m.group(3)).strip()
+        for name in m.group(4).split(","):  # a declaration may list several fields
+            d = re.match(r"\s*(\w+)\s*(?:\[(\d+)\])?\s*$", name)
+            assert d, decl
+            out.append((d.group(1), C_TYPES[ctype], int(d.group(2) or 1)))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("csl_plan_options", "PlanOptions"), ("csl_solve_info", "SolveInfo"),
+                                          ("csl_system_desc", "SystemDesc"), ("csl_paradiag_info", "ParaDiagInfo"),
+                                          ("csl_helmholtz_info", "HelmholtzInfo")])
+def test_binding_structs_match_the_header(csl, cname, pyname):
+    """The ctypes mirrors carry the header's fields in order, with the same
+    types and array lengths, so the struct sizes and offsets agree."""
+    py = getattr(csl._binding, pyname)
+    got = []
+    for fname, ftype in py._fields_:
+        n = getattr(ftype, "_length_", 1)
+        base = getattr(ftype, "_type_", ftype) if n > 1 or hasattr(ftype, "_length_") else ftype
+        got.append((fname, base, n))
+    want = header_struct(cname)
+    assert [(f, n) for f, _, n in got] == [(f, n) for f, _, n in want]
+    for (f, t_got, _), (_, t_want, _) in zip(got, want):
+        assert ctypes.sizeof(t_got) == ctypes.sizeof(t_want), (cname, f)
+
+
+def test_options_init_enables_the_fast_paths(csl):
+    o = csl._binding.PlanOptions()
+    assert csl.lib.csl_plan_options_init(ctypes.byref(o)) == 0
+    assert o.programmatic_launch == 1 and o.float_pair_stencil == 1
+    assert all(r == 0 for r in o.reserved)
