@@ -134,6 +134,31 @@ def test_K_exact_on_quadratic_3d():
     assert np.abs(O.apply_K(faces, u) - exact).max() < 1e-11
 
 
+@pytest.mark.parametrize("dim,lo_axis,hi_axis", [(2, 1, 0), (2, 0, 1), (3, 2, 1), (3, 1, 2), (3, 0, 2)])
+def test_gamma_from_faces_over_every_axis(dim, lo_axis, hi_axis):
+    # Eq. 4: gamma = sqrt(a_min a_max) with a_min, a_max over ALL face samples
+    # (reading C4).  The global minimum (0.25) sits only in the faces of
+    # lo_axis and the global maximum (9.0) only in those of hi_axis; every
+    # other sample is 2.0, so gamma = sqrt(0.25 * 9) = 1.5 exactly.  A min or
+    # max taken over one axis's faces gives 0.25*2, 2*9 or 2*2 under the root.
+    n = 3
+    shape = (n,) * dim
+    faces = []
+    for a in range(dim):
+        s = list(shape)
+        s[dim - 1 - a] += 1
+        faces.append(np.full(s, 2.0))
+    faces[lo_axis][(1,) * dim] = 0.25
+    faces[hi_axis][(0,) * dim] = 9.0
+    assert O.gamma_from_faces(faces) == 1.5
+    # Lemma 2.3 with these a_min, a_max: the generalised eigenvalues of (K, L)
+    # lie in [0.25, 9] and the bounds are not met by the 2.0 samples alone
+    if dim == 2:
+        ev = scipy.linalg.eigh(O.assemble_K_dense(faces), O.assemble_L_dense(shape), eigvals_only=True)
+        assert ev.min() >= 0.25 - 1e-12 and ev.max() <= 9.0 + 1e-12
+        assert ev.min() < 2.0 - 1e-3 and ev.max() > 2.0 + 1e-3
+
+
 def test_lemma23_rayleigh_bounds():
     # Lemma 2.3: a_min L <= K <= a_max L and L >= c0 I
     n = 15
