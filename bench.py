@@ -349,6 +349,9 @@ def main():
     ap.add_argument("--no-config2", action="store_true", help="skip the config-2 forms (FFT vs tensor-core DST)")
     ap.add_argument("--no-paradiag", action="store_true", help="skip the all-at-once time-solve line")
     ap.add_argument("--no-tables", action="store_true", help="skip the paper's table rows at n = 1023, 4095, 16383")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: loaded before the plans are made when it exists, "
+                         "written after them, so that a later (e.g. profiled) run takes the same shapes")
     ap.add_argument("--profile", choices=["config1", "config2"], default=None,
                     help="solve once, then launch each kernel of one MINRES iteration inside an "
                          "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32 "
@@ -358,8 +361,14 @@ def main():
 
     rank, world, local_rank, dist = init_replicas("nccl")
 
+    if args.tune_cache and args.impl == "csl":
+        import paper_2408_00488_gb300 as csl
+        if os.path.exists(args.tune_cache):
+            csl.tune_cache_load(args.tune_cache)
     if args.profile:
         run_profile(args.profile)
+        if args.tune_cache:
+            csl.tune_cache_save(args.tune_cache)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -417,6 +426,8 @@ def main():
         for _ in range(args.warmup):
             _, info = plans[prec].solve(f, tol=TOL, maxit=MAXIT, out=z)
         assert info.converged and info.relres <= TOL, (prec, info)
+    if args.tune_cache:
+        csl.tune_cache_save(args.tune_cache)
 
     gpu_id = "0"
     try:

@@ -75,8 +75,13 @@ typedef enum csl_precision {
                           the sine matrix of Section 2.3: operands split into two bf16 terms,
                           3 products accumulated in FP32 (relative error about 1e-5).
                           The paper has no such form (it ran FP64 throughout). */
-  CSL_PREC_BF16X6 = 3  /* as CSL_PREC_BF16X3 with three bf16 terms and 6 products
+  CSL_PREC_BF16X6 = 3, /* as CSL_PREC_BF16X3 with three bf16 terms and 6 products
                           (about FP32 accuracy) */
+  CSL_PREC_FP32_PRECOND = 4 /* FP32 only inside P^{-1} (sine transforms and per-mode
+                          scale); the stencil (matvec), the Lanczos vectors and step,
+                          the w/x update, the Givens rotations, the reductions and the
+                          true-residual check in FP64, as in CSL_PREC_FP64.  z = P^{-1} v
+                          is kept in FP32, the precision it is computed in */
 } csl_precision;
 
 typedef struct csl_plan_options {
@@ -95,7 +100,23 @@ typedef struct csl_plan_options {
                              (K + alpha I) z in float-pair arithmetic in difference form
                              (used while every face a/h^2, alpha and beta lie in
                              [2^-60, 2^60]); 0: FP64 arithmetic, direct form               */
-  int reserved[5];
+  int update_mode;         /* where the MINRES w/x update of an iteration runs: 0 (default) or
+                             1: its own kernel on a side branch beside the inverse x transform;
+                             2: fused into the inverse x transform; 3: its own kernel after
+                             the inverse x transform (batches always fuse)                  */
+  int body_iters;          /* MINRES iterations per body of the CUDA graph's WHILE loop: 0
+                             (default) = 2, else 2, 4 or 8 (more amortise the loop's
+                             per-body cost; up to body_iters - 1 iterations after
+                             convergence then exit at entry)                              */
+  int warm_start;          /* 1: csl_solve / csl_adjoint / csl_solve_host read their output
+                             vector z (y) on entry as the initial guess x_0 and run MINRES on
+                             the correction (r_0 = f - (K + lambda I) x_0); the stopping
+                             test stays relative to ||f||.  0 (default): x_0 = 0.  Single
+                             plans only (csl_batch_create refuses it)                     */
+  int history;             /* > 0: record the MINRES residual estimate |eta_j| / |eta_0|
+                             (P^{-1}-norm, non-increasing) of up to `history` iterations;
+                             read with csl_solve_history.  0 (default): none             */
+  int reserved[1];
 } csl_plan_options;
 
 typedef struct csl_solve_info {
@@ -139,7 +160,6 @@ void csl_plan_destroy(csl_plan* plan);
 /* Change the stream later calls run on. */
 csl_status csl_plan_set_stream(csl_plan* plan, void* stream);
 
-/* Device bytes owned by the plan. */
 /*
  * All-at-once time solve (the setting Section 1 gives for the shifted
  * systems; a growth row of this library, not an algorithm of the paper).
@@ -206,10 +226,25 @@ csl_status csl_helmholtz_solve(csl_helmholtz* h, const double* f, double* u, dou
                                double inner_tol, int inner_maxit, csl_helmholtz_info* info);
 void csl_helmholtz_destroy(csl_helmholtz* h);
 
+/* Device bytes owned by the plan. */
 size_t csl_plan_workspace_bytes(const csl_plan* plan);
 
 /* Human-readable launch configuration the plan chose (autotuned or default). */
 const char* csl_plan_config(const csl_plan* plan);
+
+/*
+ * The autotuner's cache (not part of the method).  Plans tune each sine-
+ * transform pass by timing its candidate shapes and keep the result per
+ * process.  csl_tune_cache_save writes every shape tuned so far to the text
+ * file `path`; csl_tune_cache_load merges the shapes of such a file into the
+ * cache, so that plans created later in this process take them without
+ * timing (e.g. a profiled process runs the shapes a benchmark chose).
+ * Loading checks every entry and loads nothing from a malformed file.
+ * Returns CSL_INVALID_ARG (message in csl_last_error()) when the file cannot
+ * be opened, written or parsed.
+ */
+csl_status csl_tune_cache_save(const char* path);
+csl_status csl_tune_cache_load(const char* path);
 
 /* gamma actually used by P (Eq. 4). */
 double csl_plan_gamma(const csl_plan* plan);
@@ -232,13 +267,21 @@ csl_status csl_precondition(csl_plan* plan, const double* v, double* out);
 
 /*
  * Solve (K + lambda I) z = f (Eq. 1) by preconditioned MINRES on Eq. 2 with P
- * (Eq. 4), zero initial guess, until the true relative residual is <= tol or
- * maxit iterations.  f, z: complex128, M entries, may not overlap.  info may
+ * (Eq. 4), zero initial guess (or z's contents with the warm_start option),
+ * until the true relative residual is <= tol or maxit iterations.  f, z: complex128, M entries, may not overlap.  info may
  * be NULL.  Returns CSL_OK, CSL_NOT_CONVERGED (z = last iterate),
  * CSL_BREAKDOWN, or an argument/CUDA error.  Synchronises the plan's stream.
  */
 csl_status csl_solve(csl_plan* plan, const double* f, double* z, double tol, int maxit,
                      csl_solve_info* info);
+
+/*
+ * The residual history of the plan's last solve (plan option `history`):
+ * copies min(iterations, history, cap) values |eta_j| / |eta_0| (j = 1, 2,
+ * ...) to out_host and their number to *count.  Synchronises the stream.
+ * CSL_INVALID_ARG when the plan records no history.
+ */
+csl_status csl_solve_history(csl_plan* plan, double* out_host, int cap, int* count);
 
 /*
  * The same solve with HOST buffers: f_host is copied to the device, solved,
@@ -303,19 +346,25 @@ size_t csl_batch_workspace_bytes(const csl_batch* batch);
  * Allocation-free P^{-1} v (the paper has no counterpart; a deployment
  * convenience).  Same result as csl_precondition on a plan built with the
  * same grid, gamma, alpha, beta and precision, but without a plan and without
- * allocating: for callers that cannot call cudaMalloc (a memory-pool-managed
- * runtime that owns all device memory, a fixed-budget embedded service, or
- * code running while a stream is being captured).
+ * allocating device memory: for callers that cannot call cudaMalloc, such as
+ * a runtime whose memory pool owns all device memory or a fixed-budget
+ * embedded service.
  *   dim, n[3]   grid (n[d] + 1 a power of two in [4, 1024]); at most 262144
  *               grid points (e.g. 511 x 511, 63 x 63 x 63), else
  *               CSL_UNSUPPORTED_SIZE with a message in csl_last_error()
- *   gamma       the averaged coefficient of Eq. 4 (> 0); alpha, beta: lambda
+ *   gamma       the averaged coefficient, as csl_plan_create computes it (> 0);
+ *               alpha, beta: lambda
  *   precision   CSL_PREC_FP64 or CSL_PREC_FP32 (as csl_plan_options.precision)
  *   v, out      device block-pair (or complex128) vectors of the grid; may alias
  *   stream      cudaStream_t as void*; the call is stream-ordered, asynchronous
- * Scratch (about 6 MiB) lives in static device arrays of the library, held by
- * every GPU that loads it until the process exits and shared by all calls:
- * calls that overlap on the GPU race and must be serialised by the caller.
+ * Returns CSL_SINGULAR_PRECOND when (gamma mu + alpha)^2 + beta^2 vanishes
+ * for some mode (to within rounding; only possible for beta = 0) and, for
+ * CSL_PREC_FP32, CSL_INVALID_ARG when the per-mode scales leave the FP32
+ * range, as csl_plan_create does; both are decided on the host before any
+ * launch.  Scratch (about 6 MiB) lives in static device arrays of the
+ * library, held by every GPU that loads it until the process exits and
+ * shared by all calls: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Every call rewrites all the scratch it reads.
  * The first call on a device performs a one-time set-up (looking up the
  * arrays' device addresses) and should come before any stream capture.
  */
@@ -324,10 +373,12 @@ csl_status csl_precondition_static(int dim, const int64_t n[3], double gamma, do
 
 /*
  * Measurement hook (not part of the method): time each kernel of one MINRES
- * iteration on the plan's stream with CUDA events, `reps` launches each,
- * against a scratch copy of the solver state so that no kernel exits early.
- * The vectors hold whatever the last call left (run a solve first).  On
- * return ms[i] is the mean duration of kernel i and names[i] its name, for
+ * iteration on the plan's stream with CUDA events, against a scratch copy of
+ * the solver state so that no kernel exits early.  Each of the `reps` timed
+ * groups is 4 back-to-back launches of the kernel between two events (the
+ * host's submission latency is then not counted).  The vectors hold whatever
+ * the last call left (run a solve first).  On return ms[i] is the mean
+ * duration of one launch of kernel i and names[i] its name, for
  * i < *count (<= 8).  Synchronises the stream.
  */
 csl_status csl_time_kernels(csl_plan* plan, int reps, double ms[8], const char* names[8], int* count);

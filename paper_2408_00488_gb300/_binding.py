@@ -8,20 +8,25 @@ import os
 from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libcsl.so")
 
 OK, INVALID_ARG, UNSUPPORTED_SIZE, SINGULAR_PRECOND, BREAKDOWN, NOT_CONVERGED, TIMEOUT, CUDA_ERROR, \
     OUT_OF_MEMORY = range(9)
-PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3
-_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16X6, PREC_FP32_PRECOND = 0, 1, 2, 3, 4
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_FP32, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6,
+         "fp32_precond": PREC_FP32_PRECOND}
 
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gamma_override", ctypes.c_double),
                 ("lines_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("programmatic_launch", ctypes.c_int),
-                ("float_pair_stencil", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("float_pair_stencil", ctypes.c_int), ("update_mode", ctypes.c_int),
+                ("body_iters", ctypes.c_int), ("warm_start", ctypes.c_int), ("history", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -78,6 +83,8 @@ _SIGS = {
     "csl_precondition": (ctypes.c_int, [_P, _P, _P]),
     "csl_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
     "csl_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+    "csl_solve_history": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "csl_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
     "csl_coef_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
     "csl_precondition_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
@@ -88,6 +95,8 @@ _SIGS = {
                                        ctypes.POINTER(SolveInfo)]),
     "csl_batch_destroy": (None, [_P]),
     "csl_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "csl_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "csl_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     "csl_time_kernels": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]),
 }
@@ -183,7 +192,8 @@ class Plan:
     def __init__(self, faces: Sequence, lam: complex, precision: str = "fp64",
                  gamma: Optional[float] = None, lines_per_cta: int = 0, use_graph: bool = True,
                  autotune: bool = True, stream=None, programmatic_launch: bool = True,
-                 float_pair_stencil: bool = True):
+                 float_pair_stencil: bool = True, update_mode: int = 0, body_iters: int = 0,
+                 warm_start: bool = False, history: int = 0):
         torch = _torch()
         dim = len(faces)
         if dim not in (2, 3):
@@ -210,6 +220,11 @@ class Plan:
         opt.autotune = 1 if autotune else 0
         opt.programmatic_launch = 1 if programmatic_launch else 0
         opt.float_pair_stencil = 1 if float_pair_stencil else 0
+        opt.update_mode = int(update_mode)
+        opt.body_iters = int(body_iters)
+        opt.warm_start = 1 if warm_start else 0
+        opt.history = int(history)
+        self.warm_start = bool(warm_start)
         self.precision = precision
         h = _P()
         st = lib.csl_plan_create(ctypes.byref(h), dim, n, ptrs, self.lam.real, self.lam.imag,
@@ -253,9 +268,18 @@ class Plan:
         return lib.csl_plan_workspace_bytes(self._h)
 
     # -- operations ----------------------------------------------------------
+    def _check_grid(self, t, what: str, pairs_ok: bool = False):
+        """The library reads and writes whole grid vectors through plain
+        pointers, so every tensor passed must hold exactly one grid vector."""
+        shape = _grid_vector(t, what) if pairs_ok else tuple(t.shape)
+        if int(np.prod(shape)) != self.M:
+            raise ValueError(f"{what} must hold one grid vector of {self.M} points (grid {self.shape}), "
+                             f"got shape {tuple(t.shape)}")
+
     def apply(self, z):
         """(K + lambda I) z for a complex128 CUDA tensor of the grid's shape."""
         torch = _torch()
+        self._check_grid(z, "z")
         self._sync_stream()
         out = torch.empty_like(z)
         _check(lib.csl_apply(self._h, _dptr(z, ("complex128",), "z"), out.data_ptr()), "csl_apply")
@@ -264,16 +288,31 @@ class Plan:
     def precondition(self, v):
         """P^{-1} v for a complex128 (or (...,2) float64) CUDA tensor."""
         torch = _torch()
+        self._check_grid(v, "v", pairs_ok=True)
         self._sync_stream()
         out = torch.empty_like(v)
         _check(lib.csl_precondition(self._h, _dptr(v, ("complex128", "float64"), "v"), out.data_ptr()),
                "csl_precondition")
         return out
 
-    def solve(self, f, tol: float = 1e-8, maxit: int = 1000, out=None) -> Tuple[object, Info]:
+    def solve(self, f, tol: float = 1e-8, maxit: int = 1000, out=None, x0=None) -> Tuple[object, Info]:
+        """Solve (K + lambda I) z = f.  x0 (plans made with warm_start=True):
+        the initial guess, copied into the output before the call (the
+        library reads the output vector as x0)."""
         torch = _torch()
+        self._check_grid(f, "f")
+        if out is not None:
+            self._check_grid(out, "out")
         self._sync_stream()
         z = torch.empty_like(f) if out is None else out
+        if self.warm_start:
+            if x0 is None:
+                z.zero_()
+            elif x0 is not z:
+                self._check_grid(x0, "x0")
+                z.copy_(x0)
+        elif x0 is not None:
+            raise ValueError("x0 needs a plan made with warm_start=True")
         ci = SolveInfo()
         st = lib.csl_solve(self._h, _dptr(f, ("complex128",), "f"), _dptr(z, ("complex128",), "z"),
                            float(tol), int(maxit), ctypes.byref(ci))
@@ -282,8 +321,13 @@ class Plan:
 
     def adjoint(self, g, tol: float = 1e-8, maxit: int = 1000, out=None):
         torch = _torch()
+        self._check_grid(g, "g")
+        if out is not None:
+            self._check_grid(out, "out")
         self._sync_stream()
         y = torch.empty_like(g) if out is None else out
+        if self.warm_start and out is None:
+            y.zero_()  # no initial guess given: start from 0
         ci = SolveInfo()
         st = lib.csl_adjoint(self._h, _dptr(g, ("complex128",), "g"), _dptr(y, ("complex128",), "y"),
                              float(tol), int(maxit), ctypes.byref(ci))
@@ -292,6 +336,9 @@ class Plan:
 
     def solve_host(self, f_host, z_host, tol: float = 1e-8, maxit: int = 1000) -> Info:
         """Solve with host (CPU, ideally pinned) complex128 tensors/arrays."""
+        for t, what in ((f_host, "f_host"), (z_host, "z_host")):
+            if int(np.prod(tuple(t.shape))) != self.M or "complex128" not in str(t.dtype):
+                raise ValueError(f"{what} must be a complex128 host array of {self.M} points")
         self._sync_stream()
         ci = SolveInfo()
         fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data
@@ -299,6 +346,14 @@ class Plan:
         st = lib.csl_solve_host(self._h, fp, zp, float(tol), int(maxit), ctypes.byref(ci))
         _check(st, "csl_solve_host", allow=(OK, NOT_CONVERGED, BREAKDOWN))
         return Info.from_c(ci)
+
+    def history(self, cap: int = 100000):
+        """|eta_j| / |eta_0| of each iteration of the last solve (plans made
+        with history > 0): the MINRES residual estimate in the P^{-1}-norm."""
+        buf = (ctypes.c_double * max(1, int(cap)))()
+        cnt = ctypes.c_int(0)
+        _check(lib.csl_solve_history(self._h, buf, int(cap), ctypes.byref(cnt)), "csl_solve_history")
+        return [buf[i] for i in range(cnt.value)]
 
     def time_kernels(self, reps: int = 10):
         """{kernel name: mean ms per launch} for the kernels of one iteration
@@ -315,6 +370,8 @@ class Plan:
 
     def coef_grad(self, z, y):
         torch = _torch()
+        self._check_grid(z, "z")
+        self._check_grid(y, "y")
         self._sync_stream()
         nz, ny, nx = (1,) + self.shape if self.dim == 2 else self.shape
         shapes = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][: self.dim]
@@ -379,6 +436,12 @@ class Batch:
 
     def solve(self, fs, tol: float = 1e-8, maxit: int = 1000, outs=None):
         torch = _torch()
+        if len(fs) != self.n or (outs is not None and len(outs) != self.n):
+            raise ValueError(f"one right-hand side (and output) per system: {self.n}")
+        for i, shp in enumerate(self.shapes):
+            for t in [fs[i]] + ([outs[i]] if outs is not None else []):
+                if int(np.prod(tuple(t.shape))) != int(np.prod(shp)):
+                    raise ValueError(f"system {i}: a vector of grid {shp} expected, got shape {tuple(t.shape)}")
         zs = [torch.empty_like(f) for f in fs] if outs is None else outs
         fp = (_P * self.n)(*[_dptr(f, ("complex128",), "f") for f in fs])
         zp = (_P * self.n)(*[_dptr(z, ("complex128",), "z") for z in zs])
@@ -388,20 +451,59 @@ class Batch:
         return zs, [Info.from_c(infos[i]) for i in range(self.n)]
 
 
+def tune_cache_save(path: str) -> None:
+    """Write the autotuner's shapes tuned so far in this process to `path`."""
+    _check(lib.csl_tune_cache_save(os.fsencode(path)), "csl_tune_cache_save")
+
+
+def tune_cache_load(path: str) -> None:
+    """Merge the shapes of a file written by tune_cache_save into the
+    autotuner's cache (plans created afterwards take them without timing)."""
+    _check(lib.csl_tune_cache_load(os.fsencode(path)), "csl_tune_cache_load")
+
+
+def _grid_vector(v, what: str):
+    """The grid shape of a vector passed as complex128 (grid shape) or as
+    float64 block pairs (grid shape + (2,))."""
+    name = str(v.dtype).replace("torch.", "")
+    if name == "complex128":
+        return tuple(v.shape)
+    if name == "float64":
+        if v.dim() < 1 or v.shape[-1] != 2:
+            raise ValueError(f"{what}: a float64 vector holds block pairs and needs a trailing dimension of 2, "
+                             f"got shape {tuple(v.shape)}")
+        return tuple(v.shape[:-1])
+    raise ValueError(f"{what} must be complex128 or float64 block pairs, got {v.dtype}")
+
+
 def precondition_static(v, gamma: float, lam: complex, precision: str = "fp64", out=None, stream=None):
-    """P^{-1} v without a plan and without any device allocation
-    (csl_precondition_static): for callers that cannot allocate device memory.
-    v: complex128 CUDA tensor of the grid's shape (2D or 3D, at most 262144
-    points); gamma: the averaged coefficient of P; lam: the shift."""
+    """P^{-1} v without a plan and without any device allocation by the
+    library (csl_precondition_static): for callers that cannot allocate device
+    memory themselves.  v: complex128 CUDA tensor of the grid's shape (2D or
+    3D, at most 262144 points), or float64 block pairs of shape grid + (2,);
+    gamma: the averaged coefficient of P; lam: the shift.  `out` (same shape,
+    dtype and device as v) receives the result; without it one is allocated
+    here by PyTorch."""
     torch = _torch()
-    dim = v.dim()
-    shape = tuple(v.shape)
+    shape = _grid_vector(v, "v")
+    dim = len(shape)
+    if dim not in (2, 3):
+        raise ValueError(f"v must describe a 2D or 3D grid, got grid shape {shape}")
+    if out is None:
+        y = torch.empty_like(v)
+    else:
+        if tuple(out.shape) != tuple(v.shape) or out.dtype != v.dtype:
+            raise ValueError(f"out must have v's shape {tuple(v.shape)} and dtype {v.dtype}")
+        if out.device != v.device:
+            raise ValueError("out must be on v's device")
+        y = out
     n = (ctypes.c_int64 * 3)(*(list(reversed(shape)) + [1] * (3 - dim)))
-    y = torch.empty_like(v) if out is None else out
     lam = complex(lam)
-    st = lib.csl_precondition_static(dim, n, float(gamma), lam.real, lam.imag, _PREC[precision],
-                                     _dptr(v, ("complex128", "float64"), "v"), _dptr(y, ("complex128", "float64"), "out"),
-                                     _stream_handle(stream))
+    with torch.cuda.device(v.device):
+        sh = _stream_handle(stream if stream is not None else torch.cuda.current_stream(v.device))
+        st = lib.csl_precondition_static(dim, n, float(gamma), lam.real, lam.imag, _PREC[precision],
+                                         _dptr(v, ("complex128", "float64"), "v"),
+                                         _dptr(y, ("complex128", "float64"), "out"), sh)
     _check(st, "csl_precondition_static")
     return y
 
@@ -470,6 +572,10 @@ class ParaDiag:
     def solve(self, u0, g, tol: float = 1e-10, maxit: int = 20, inner_tol: float = 1e-12, inner_maxit: int = 2000,
               out=None):
         torch = _torch()
+        if tuple(u0.shape) != self.shape or tuple(g.shape) != (self.L,) + self.shape:
+            raise ValueError(f"u0 must have shape {self.shape} and g shape {(self.L,) + self.shape}")
+        if out is not None and tuple(out.shape) != tuple(g.shape):
+            raise ValueError("out must have g's shape")
         u = torch.empty_like(g) if out is None else out
         info = ParaDiagInfo()
         st = lib.csl_paradiag_solve(self._h, _dptr(u0.contiguous(), ("complex128",), "u0"),
@@ -524,6 +630,8 @@ class Helmholtz:
     def solve(self, f, tol: float = 1e-8, maxit: int = 500, inner_tol: float = 1e-6, inner_maxit: int = 2000,
               out=None):
         torch = _torch()
+        if tuple(f.shape) != self.shape or (out is not None and tuple(out.shape) != self.shape):
+            raise ValueError(f"f (and out) must have the grid's shape {self.shape}")
         u = torch.empty_like(f) if out is None else out
         info = HelmholtzInfo()
         st = lib.csl_helmholtz_solve(self._h, _dptr(f.contiguous(), ("complex128",), "f"),

@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/csl.h"
 #include "../../include/csl_testing.h"
 #include "csl_kernels.cuh"
@@ -20,6 +22,15 @@ using namespace csl;
 
 namespace {
 thread_local char g_last_error[512] = "";
+
+// NVTX range for the life of a scope (named per entry point and phase, so
+// that a profiler can select a solve, its prologue or its loop)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 void record_error(cudaError_t e, const char* what, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s failed at csl_api.cu:%d: %s (%s)", what, line,
            cudaGetErrorName(e), cudaGetErrorString(e));
@@ -111,6 +122,7 @@ struct csl_plan {
   int use_graph = 1;
   int use_pdl = 1;  // programmatic dependent launch of the iteration's kernels
   int ff = 0;       // FP32-preconditioner forms: float-pair stencil (faces in cxp/cyp/czp)
+  int vpair = 0;    // v, w and x stored as float pairs (CSL_PREC_FP32 and the split-BF16 forms)
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   // the w/x update of an iteration runs on a side branch beside the inverse
@@ -118,6 +130,8 @@ struct csl_plan {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int split_update = 1;
+  int serial_update = 0;  // update_mode 3: the update kernel after the inverse x transform, same stream
+  int body_iters = 2;     // MINRES iterations per WHILE body of the graph
   int upd_blocks = 1;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -132,6 +146,10 @@ struct csl_plan {
   void* sine_tc[3] = {nullptr, nullptr, nullptr};  // tensor-core passes: split-bf16 sine matrix per axis
   int tc_split = 0;                                // 2 or 3 bf16 terms (CSL_PREC_BF16X3 / X6), else 0
   double2 *b = nullptr, *x = nullptr, *io = nullptr;
+  double2* x0 = nullptr;       // warm start: the caller's initial guess
+  int warm = 0;
+  double* hist = nullptr;      // residual history (plan option `history`)
+  int hist_cap = 0;
   double2* v[2] = {nullptr, nullptr};
   double2* w[2] = {nullptr, nullptr};
   void* z[2] = {nullptr, nullptr};
@@ -290,6 +308,10 @@ RowArgs<T> row_args(csl_plan* P) {
   return a;
 }
 
+// row-pass modes of the Lanczos step and the fused update for the plan's vector storage
+inline int lanczos_load(const csl_plan* P) { return P->vpair ? LOAD_LANCZOS : LOAD_LANCZOS_V64; }
+inline int update_store(const csl_plan* P) { return P->vpair ? STORE_Z_UPDATE : STORE_Z_UPDATE_V64; }
+
 template <typename T>
 StridedArgs<T> strided_args(csl_plan* P, const PassCfg& c, int axis) {
   StridedArgs<T> a;
@@ -382,13 +404,15 @@ StencilArgs stencil_args(const csl_plan* P, int par) {
 
 typedef void (*StencilFn)(StencilArgs, const StencilArgs*, int);
 
-// the stencil kernel for the plan's form (float pairs only with an FP32 ẑ)
+// the stencil kernel for the plan's form: float-pair arithmetic (ff) and
+// pair-stored vectors (vp) only with an FP32 ẑ
 template <typename TZ>
-StencilFn stencil_fn(int dim, bool ff) {
+StencilFn stencil_fn(int dim, bool ff, bool vp) {
   if constexpr (sizeof(TZ) == 8) {
-    if (ff) return dim == 2 ? k_stencil<2, TZ, true> : k_stencil<3, TZ, true>;
+    if (ff) return dim == 2 ? k_stencil<2, TZ, true, true> : k_stencil<3, TZ, true, true>;
+    if (vp) return dim == 2 ? k_stencil<2, TZ, false, true> : k_stencil<3, TZ, false, true>;
   }
-  return dim == 2 ? k_stencil<2, TZ, false> : k_stencil<3, TZ, false>;
+  return dim == 2 ? k_stencil<2, TZ, false, false> : k_stencil<3, TZ, false, false>;
 }
 
 template <typename T>
@@ -399,7 +423,8 @@ cudaError_t launch_stencil(csl_plan* P, int par, cudaStream_t s, bool use_cond) 
   typedef typename C2<T>::t TZ;
   const StencilArgs* nob = nullptr;
   const size_t smem = (sizeof(TZ) == 8 && P->ff) ? ff_stencil_smem(P->dim) : 0;
-  return launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, P->ff != 0), P->sten_blocks, 256, smem, s, a, nob, 0);
+  return launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, P->ff != 0, P->vpair != 0), P->sten_blocks, 256, smem, s, a,
+                  nob, 0);
 }
 
 template <typename T>
@@ -435,7 +460,13 @@ cudaError_t launch_update(csl_plan* P, int par, cudaStream_t s) {
   u.x = P->x;
   u.st = P->st;
   u.M = P->M;
-  k_update<typename C2<T>::t><<<P->upd_blocks, 256, 0, s>>>(u);
+  if constexpr (sizeof(T) == 4) {
+    if (P->vpair) {
+      k_update<float2, true><<<P->upd_blocks, 256, 0, s>>>(u);
+      return cudaGetLastError();
+    }
+  }
+  k_update<typename C2<T>::t, false><<<P->upd_blocks, 256, 0, s>>>(u);
   return cudaGetLastError();
 }
 
@@ -443,10 +474,15 @@ cudaError_t launch_update(csl_plan* P, int par, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_iteration_T(csl_plan* P, int par, cudaStream_t s, bool use_cond) {
   cudaError_t e = launch_stencil<T>(P, par, s, use_cond);
-  if (e == cudaSuccess) e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, par), s);
+  if (e == cudaSuccess) e = run_row<T>(P, lanczos_load(P), STORE_T, p1_args<T>(P, par), s);
   if (e == cudaSuccess) e = launch_mid_chain<T>(P, s, P->st, 2);
   if (!P->split_update) {
-    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z_UPDATE, p3_args<T>(P, par), s);
+    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, update_store(P), p3_args<T>(P, par), s);
+    return e;
+  }
+  if (P->serial_update) {
+    if (e == cudaSuccess) e = run_row<T>(P, LOAD_T, STORE_Z, p3_args<T>(P, par), s);
+    if (e == cudaSuccess) e = launch_update<T>(P, par, s);
     return e;
   }
   // fork: the update on the side stream, the inverse x transform (z_{j+1})
@@ -485,9 +521,31 @@ cudaError_t launch_prologue_T(csl_plan* P, const double2* f, double tol, int max
   ia.maxit = maxit;
   ia.sqrt_pmin = P->sqrt_pmin;
   ia.sqrt_pmax = P->sqrt_pmax;
-  ia.vpair = sizeof(T) == 4 ? 1 : 0;
+  ia.vpair = P->vpair;
   k_ingest<<<P->ew_blocks, 256, 0, s>>>(ia, nullptr, 0);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && P->warm) {
+    WarmArgs wa;
+    wa.g.nx = P->n[0];
+    wa.g.ny = P->n[1];
+    wa.g.nz = P->dim == 3 ? P->n[2] : 1;
+    wa.g.M = P->M;
+    wa.x0 = P->x0;
+    wa.b = P->b;
+    wa.v0 = P->v[0];
+    wa.cx = P->cx;
+    wa.cy = P->cy;
+    wa.cz = P->cz;
+    wa.dg = P->dg;
+    wa.st = P->st;
+    wa.partials = P->partials;
+    wa.vpair = P->vpair;
+    if (P->dim == 2)
+      k_warm_start<2><<<P->ew_blocks, 256, 0, s>>>(wa);
+    else
+      k_warm_start<3><<<P->ew_blocks, 256, 0, s>>>(wa);
+    e = cudaGetLastError();
+  }
   RowArgs<T> r1 = row_args<T>(P);
   r1.vin = P->b;  // v_1 = b (v[0] holds it as pairs in the FP32 forms)
   r1.tout = (typename C2<T>::t*)P->T;
@@ -547,10 +605,10 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
   if (kind == 0) {
     const PassCfg keep = P->row;
     P->row = c;
-    cudaError_t e = run_row<T>(P, LOAD_LANCZOS, STORE_T, p1_args<T>(P, 0), P->stream);
+    cudaError_t e = run_row<T>(P, lanczos_load(P), STORE_T, p1_args<T>(P, 0), P->stream);
     // P3 as the solve runs it (the update on its own branch, or fused)
     if (e == cudaSuccess)
-      e = run_row<T>(P, LOAD_T, P->split_update ? STORE_Z : STORE_Z_UPDATE, p3_args<T>(P, 0), P->stream);
+      e = run_row<T>(P, LOAD_T, P->split_update ? STORE_Z : update_store(P), p3_args<T>(P, 0), P->stream);
     P->row = keep;
     return e;
   }
@@ -565,6 +623,33 @@ cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
   return launch_strided<T>(c.N, c.wide, kind == 2, a, c.L, P->stream);
 }
 
+// One candidate shape of a pass: transform variant w with `lines` lines per
+// CTA; false when the shape is not allowed (CTA size, shared memory, tile
+// wider than twice the grid's x extent).  Used by the tuner and by the cache
+// loader, so a shape read from a file is rebuilt and checked the same way.
+template <typename T>
+bool make_candidate(const PassCfg& c, int kind, int w, int lines, PassCfg& cand) {
+  if (w < 0 || w >= pass_num_variants(c.N) || lines < 1 || (lines & (lines - 1))) return false;
+  const int tpl = pass_tpl(c.N, w);
+  if (lines * tpl < 32 || lines * tpl > 256) return false;
+  cand = c;
+  cand.wide = w;
+  cand.lines = lines;
+  cand.L.threads = lines * tpl;
+  cand.L.smem = pass_smem<T>(c.N, cand.wide, lines);
+  if (cand.L.smem > 200 * 1024) return false;
+  long tiles;
+  if (kind == 0) {
+    tiles = (c.nouter + lines - 1) / lines;
+    cand.L.blocks = (int)(tiles < (long)kSMs * 16 ? tiles : (long)kSMs * 16);
+  } else {
+    if (lines > 2 * c.ncols) return false;
+    tiles = (long)((c.ncols + lines - 1) / lines) * c.nouter;
+    cand.L.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
+  }
+  return true;
+}
+
 template <typename T>
 cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e0, cudaEvent_t e1,
                       const DevState& hst) {
@@ -574,31 +659,21 @@ cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      c = it->second;
-      return cudaSuccess;
+      PassCfg hit;
+      // a cached shape is rebuilt from (variant, lines) for this plan's pass
+      if (make_candidate<T>(c, kind, it->second.wide, it->second.lines, hit)) {
+        hit.L.pdl = c.L.pdl;
+        c = hit;
+        return cudaSuccess;
+      }
     }
   }
   PassCfg best = c;
   float best_ms = 1e30f;
   for (int w = 0; w < pass_num_variants(c.N); ++w) {
-    const int tpl = pass_tpl(c.N, w);
-    for (int lines = 1; lines * tpl <= 256; lines <<= 1) {
-      if (lines * tpl < 32) continue;
-      PassCfg cand = c;
-      cand.wide = w;
-      cand.lines = lines;
-      cand.L.threads = lines * tpl;
-      cand.L.smem = pass_smem<T>(c.N, cand.wide, lines);
-      if (cand.L.smem > 200 * 1024) continue;
-      long tiles;
-      if (kind == 0) {
-        tiles = (c.nouter + lines - 1) / lines;
-        cand.L.blocks = (int)(tiles < (long)kSMs * 16 ? tiles : (long)kSMs * 16);
-      } else {
-        if (lines > 2 * c.ncols) continue;
-        tiles = (long)((c.ncols + lines - 1) / lines) * c.nouter;
-        cand.L.blocks = (int)(tiles < kMaxRedBlocks ? tiles : kMaxRedBlocks);
-      }
+    for (int lines = 1; lines <= 256; lines <<= 1) {
+      PassCfg cand;
+      if (!make_candidate<T>(c, kind, w, lines, cand)) continue;
       // the fastest of 5 timed groups (after one warm-up) of 3 back-to-back
       // launches: the host's submission hides behind the GPU's execution, and
       // a group delayed by something else on the GPU is discarded
@@ -663,6 +738,20 @@ cudaError_t autotune(csl_plan* P) {
   return e;
 }
 
+// The tuner's cache as a text file: a header line, then one line per tuned
+// pass "prec kind N ncols nouter variant lines".  Only (variant, lines) are
+// kept; the launch shape is rebuilt from them when a plan asks for that pass.
+const char* kTuneHeader = "csl-tune-cache 1";
+
+bool tune_entry_valid(const TuneKey& k, int wide, int lines) {
+  if (k.prec != 4 && k.prec != 8) return false;
+  if (k.kind < 0 || k.kind > 2) return false;
+  if (k.N < 4 || k.N > 1024 || ilog2_exact(k.N) < 0) return false;
+  if (k.ncols < 1 || k.nouter < 1) return false;
+  if (wide < 0 || wide >= pass_num_variants(k.N)) return false;
+  return lines >= 1 && lines <= 256 && !(lines & (lines - 1));
+}
+
 // Build the graph: one WHILE node whose body is two MINRES iterations (both
 // buffer parities); the stencil kernel's last block sets the condition.
 void build_graph(csl_plan* P) {
@@ -683,8 +772,8 @@ void build_graph(csl_plan* P) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = launch_iteration(P, 0, P->cap, true);
-      if (e1 == cudaSuccess) e1 = launch_iteration(P, 1, P->cap, true);
+      cudaError_t e1 = cudaSuccess;
+      for (int k = 0; k < P->body_iters && e1 == cudaSuccess; ++k) e1 = launch_iteration(P, k & 1, P->cap, true);
       cudaGraph_t captured = body;
       e = cudaStreamEndCapture(P->cap, &captured);
       if (e == cudaSuccess) e = e1;
@@ -711,7 +800,10 @@ csl_status run_loop(csl_plan* P, int maxit) {
   // host-driven loop: batches of 8 iterations, then read the done flag
   int done = 0;
   for (int it = 0; it < maxit + 4 && !done; it += 8) {
-    for (int k = 0; k < 8; ++k) CSL_TRY(launch_iteration(P, k & 1, P->stream, false));
+    for (int k = 0; k < 8; ++k) {
+      NvtxRange r("csl:iteration");
+      CSL_TRY(launch_iteration(P, k & 1, P->stream, false));
+    }
     CSL_TRY(cudaMemcpyAsync(&done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     CSL_TRY(cudaStreamSynchronize(P->stream));
   }
@@ -735,23 +827,37 @@ csl_status read_info(csl_plan* P, csl_solve_info* info, csl_status* solve_status
     const int per_iter = P->dim == 2 ? 4 : 6;
     const int prologue = 1 + per_iter;
     const int it_launches = per_iter + (P->split_update ? 1 : 0);  // + k_update on the side branch
-    const int bodies = (h.loops + 1) / 2;
+    const int B = P->body_iters;
+    const int bodies = (h.loops + B - 1) / B;
     info->launches =
-        prologue + (P->graph_state == 1 ? bodies * 2 * it_launches : ((h.loops + 7) / 8) * 8 * it_launches);
+        prologue + (P->graph_state == 1 ? bodies * B * it_launches : ((h.loops + 7) / 8) * 8 * it_launches);
   }
   return CSL_OK;
 }
 
-// the iterate x to the caller's FP64 vector (the FP32 forms hold it as float pairs)
+// the iterate x to the caller's FP64 vector (the FP32 forms hold it as float
+// pairs; with a warm start x is the correction to x_0)
 cudaError_t copy_out(csl_plan* P, double2* dst, cudaStream_t s) {
-  if (P->precision == CSL_PREC_FP64) return cudaMemcpyAsync(dst, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, s);
+  if (P->warm) {
+    k_x_out_add<<<P->ew_blocks, 256, 0, s>>>(P->x, P->vpair, P->x0, dst, P->M);
+    return cudaGetLastError();
+  }
+  if (!P->vpair) return cudaMemcpyAsync(dst, P->x, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, s);
   k_x_out<<<P->ew_blocks, 256, 0, s>>>((const float4*)P->x, dst, P->M);
   return cudaGetLastError();
 }
 
-csl_status solve_impl(csl_plan* P, const double2* f, double tol, int maxit, double beta) {
+// x0: the caller's initial guess (device, warm-start plans), copied before the
+// prologue because the caller's buffer is also the output
+csl_status solve_impl(csl_plan* P, const double2* f, double tol, int maxit, double beta, const double2* x0) {
   if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
-  CSL_TRY(launch_prologue(P, f, tol, maxit, beta, P->stream));
+  if (P->warm && x0 && x0 != P->x0)
+    CSL_TRY(cudaMemcpyAsync(P->x0, x0, sizeof(double2) * P->M, cudaMemcpyDeviceToDevice, P->stream));
+  {
+    NvtxRange r("csl:prologue");
+    CSL_TRY(launch_prologue(P, f, tol, maxit, beta, P->stream));
+  }
+  NvtxRange r("csl:minres-loop");
   return run_loop(P, maxit);
 }
 
@@ -810,6 +916,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   csl_plan_options o;
   csl_plan_options_init(&o);
   if (opt) o = *opt;
+  if (o.history < 0 || o.history > (1 << 24)) return CSL_INVALID_ARG;
+  NvtxRange nv("csl_plan_create");
   // transform lengths: 4 .. 1024 in 2D and 3D; 2D grids up to 16384 in FP64
   // (lines of 16384 on two-CTA clusters) and 4096 in the FP32 forms, whose
   // P^{-1} error grows like eps_32 kappa(P), kappa(P) ~ n^2
@@ -819,7 +927,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     if (n[d] + 1 < 4 || n[d] + 1 > nmax || ilog2_exact(n[d] + 1) < 0) return CSL_UNSUPPORTED_SIZE;
   }
   if (o.precision != CSL_PREC_FP64 && o.precision != CSL_PREC_FP32 && o.precision != CSL_PREC_BF16X3 &&
-      o.precision != CSL_PREC_BF16X6)
+      o.precision != CSL_PREC_BF16X6 && o.precision != CSL_PREC_FP32_PRECOND)
     return CSL_INVALID_ARG;
   CSL_TRY(set_attrs_once());
 
@@ -827,8 +935,19 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   if (!P) return CSL_OUT_OF_MEMORY;
   P->dim = dim;
   P->precision = o.precision;
+  P->vpair = (o.precision == CSL_PREC_FP32 || o.precision == CSL_PREC_BF16X3 || o.precision == CSL_PREC_BF16X6) ? 1 : 0;
   P->use_graph = o.use_graph;
   P->use_pdl = o.programmatic_launch;
+  if (o.update_mode < 0 || o.update_mode > 3 ||
+      !(o.body_iters == 0 || o.body_iters == 2 || o.body_iters == 4 || o.body_iters == 8)) {
+    delete P;
+    return CSL_INVALID_ARG;
+  }
+  P->split_update = o.update_mode == 2 ? 0 : 1;
+  P->serial_update = o.update_mode == 3 ? 1 : 0;
+  P->body_iters = o.body_iters ? o.body_iters : 2;
+  P->warm = o.warm_start ? 1 : 0;
+  P->hist_cap = o.history;
   P->stream = (cudaStream_t)stream;
   P->alpha = alpha;
   P->beta = beta;
@@ -855,7 +974,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   if (dim == 3) P->cz = (double*)dalloc(P, nface[2] * 8, &err);
   P->dg = (double*)dalloc(P, M * 8, &err);
   if (o.precision == CSL_PREC_FP64) P->stab = (double*)dalloc(P, M * 8, &err);
-  if (o.precision != CSL_PREC_FP64 && o.float_pair_stencil) {
+  if (P->vpair && o.float_pair_stencil) {
     P->cxp = (float2*)dalloc(P, nface[0] * 8, &err);
     P->cyp = (float2*)dalloc(P, nface[1] * 8, &err);
     if (dim == 3) P->czp = (float2*)dalloc(P, nface[2] * 8, &err);
@@ -871,6 +990,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   P->b = (double2*)dalloc(P, M * 16, &err);
   P->x = (double2*)dalloc(P, M * 16, &err);
   P->io = (double2*)dalloc(P, M * 16, &err);
+  if (P->warm) P->x0 = (double2*)dalloc(P, M * 16, &err);
+  if (P->hist_cap > 0) P->hist = (double*)dalloc(P, (size_t)P->hist_cap * 8, &err);
   for (int i = 0; i < 2; ++i) {
     P->v[i] = (double2*)dalloc(P, M * 16, &err);
     P->w[i] = (double2*)dalloc(P, M * 16, &err);
@@ -945,7 +1066,7 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
       const float ah = (float)alpha;
       P->alpha2 = make_float2(ah, (float)(alpha - (double)ah));
       float2* pdst[3] = {P->cxp, P->cyp, P->czp};
-      if (P->ff) err = allow_dyn_smem((const void*)stencil_fn<float2>(dim, true));
+      if (P->ff) err = allow_dyn_smem((const void*)stencil_fn<float2>(dim, true, true));
       for (int d = 0; d < dim && err == cudaSuccess; ++d) {
         const int blocks = (int)((nface[d] + 255) / 256 < 1024 ? (nface[d] + 255) / 256 : 1024);
         k_pair_faces<<<blocks, 256, 0, s>>>(dst[d], pdst[d], nface[d]);
@@ -1036,6 +1157,13 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
     unsigned long long res[2] = {0, 0};
     if (err == cudaSuccess) err = cudaMemcpyAsync(res, P->u64, sizeof(res), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemsetAsync(P->st, 0, sizeof(DevState), s);
+    if (err == cudaSuccess && P->hist) {  // the history buffer, once per plan (the ingest leaves it alone)
+      DevState hs;
+      memset(&hs, 0, sizeof(hs));
+      hs.hist = P->hist;
+      hs.hist_cap = P->hist_cap;
+      err = cudaMemcpyAsync(P->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s);
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err == cudaSuccess) {
       double qmin, qmax;
@@ -1139,10 +1267,11 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   {
     const PassCfg* cs[3] = {&P->row, &P->sy, &P->sz};
     const char* nm[3] = {"x", "y", "z"};
-    const char* pname = o.precision == CSL_PREC_FP64     ? "fp64"
-                        : o.precision == CSL_PREC_FP32   ? "fp32"
-                        : o.precision == CSL_PREC_BF16X3 ? "bf16x3"
-                                                         : "bf16x6";
+    const char* pname = o.precision == CSL_PREC_FP64            ? "fp64"
+                        : o.precision == CSL_PREC_FP32          ? "fp32"
+                        : o.precision == CSL_PREC_FP32_PRECOND  ? "fp32-precond"
+                        : o.precision == CSL_PREC_BF16X3        ? "bf16x3"
+                                                                : "bf16x6";
     int off = snprintf(P->config, sizeof(P->config), "%s%s stencil[%s strip=%d blocks=%d]", pname,
                        o.autotune ? " autotuned" : "", P->ff ? "float-pair" : "fp64", P->sten_strip, P->sten_blocks);
     for (int d = 0; d < dim && off < (int)sizeof(P->config); ++d)
@@ -1163,6 +1292,58 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
 
 const char* csl_plan_config(const csl_plan* plan) { return plan ? plan->config : ""; }
 
+csl_status csl_tune_cache_save(const char* path) {
+  if (!path) return CSL_INVALID_ARG;
+  FILE* fh = fopen(path, "w");
+  if (!fh) {
+    csl_internal_set_error("csl_tune_cache_save: cannot open the file for writing");
+    return CSL_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(fh, "%s\n", kTuneHeader);
+  for (const auto& kv : g_tune_cache)
+    fprintf(fh, "%d %d %d %d %d %d %d\n", kv.first.prec, kv.first.kind, kv.first.N, kv.first.ncols,
+            kv.first.nouter, kv.second.wide, kv.second.lines);
+  const int bad = ferror(fh);
+  fclose(fh);
+  return bad ? CSL_INVALID_ARG : CSL_OK;
+}
+
+csl_status csl_tune_cache_load(const char* path) {
+  if (!path) return CSL_INVALID_ARG;
+  FILE* fh = fopen(path, "r");
+  if (!fh) {
+    csl_internal_set_error("csl_tune_cache_load: cannot open the file");
+    return CSL_INVALID_ARG;
+  }
+  char line[256];
+  if (!fgets(line, sizeof(line), fh) || strncmp(line, kTuneHeader, strlen(kTuneHeader)) != 0) {
+    fclose(fh);
+    csl_internal_set_error("csl_tune_cache_load: not a csl tuner cache file");
+    return CSL_INVALID_ARG;
+  }
+  std::vector<std::pair<TuneKey, PassCfg>> entries;
+  while (fgets(line, sizeof(line), fh)) {
+    TuneKey k;
+    int wide = 0, lines = 0;
+    if (sscanf(line, "%d %d %d %d %d %d %d", &k.prec, &k.kind, &k.N, &k.ncols, &k.nouter, &wide, &lines) != 7 ||
+        !tune_entry_valid(k, wide, lines)) {
+      fclose(fh);
+      csl_internal_set_error("csl_tune_cache_load: malformed entry; nothing was loaded");
+      return CSL_INVALID_ARG;
+    }
+    PassCfg c;
+    c.N = k.N;
+    c.wide = wide;
+    c.lines = lines;
+    entries.push_back({k, c});
+  }
+  fclose(fh);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& e : entries) g_tune_cache[e.first] = e.second;
+  return CSL_OK;
+}
+
 void csl_plan_destroy(csl_plan* plan) {
   if (!plan) return;
   cudaStreamSynchronize(plan->stream);
@@ -1181,6 +1362,7 @@ double csl_plan_gamma(const csl_plan* plan) { return plan ? plan->gamma : kNaN; 
 
 csl_status csl_apply(csl_plan* P, const double* z, double* out) {
   if (!P || !z || !out) return CSL_INVALID_ARG;
+  NvtxRange r("csl_apply");
   Grid g;
   g.nx = P->n[0];
   g.ny = P->n[1];
@@ -1198,6 +1380,7 @@ csl_status csl_apply(csl_plan* P, const double* z, double* out) {
 
 csl_status csl_precondition(csl_plan* P, const double* v, double* out) {
   if (!P || !v || !out) return CSL_INVALID_ARG;
+  NvtxRange r("csl_precondition");
   if (P->precision != CSL_PREC_FP64)
     CSL_TRY(launch_precondition_T<float>(P, (const double2*)v, (double2*)out, P->stream));
   else
@@ -1207,7 +1390,8 @@ csl_status csl_precondition(csl_plan* P, const double* v, double* out) {
 
 csl_status csl_solve(csl_plan* P, const double* f, double* z, double tol, int maxit, csl_solve_info* info) {
   if (!P || !f || !z) return CSL_INVALID_ARG;
-  csl_status s = solve_impl(P, (const double2*)f, tol, maxit, P->beta);
+  NvtxRange r("csl_solve");
+  csl_status s = solve_impl(P, (const double2*)f, tol, maxit, P->beta, (const double2*)z);
   if (s != CSL_OK) return s;
   CSL_TRY(copy_out(P, (double2*)z, P->stream));
   csl_status st = CSL_OK;
@@ -1217,7 +1401,8 @@ csl_status csl_solve(csl_plan* P, const double* f, double* z, double tol, int ma
 
 csl_status csl_adjoint(csl_plan* P, const double* g, double* y, double tol, int maxit, csl_solve_info* info) {
   if (!P || !g || !y) return CSL_INVALID_ARG;
-  csl_status s = solve_impl(P, (const double2*)g, tol, maxit, -P->beta);
+  NvtxRange r("csl_adjoint");
+  csl_status s = solve_impl(P, (const double2*)g, tol, maxit, -P->beta, (const double2*)y);
   if (s != CSL_OK) return s;
   CSL_TRY(copy_out(P, (double2*)y, P->stream));
   csl_status st = CSL_OK;
@@ -1230,14 +1415,33 @@ csl_status csl_solve_host(csl_plan* P, const double* f_host, double* z_host, dou
   if (!P || !f_host || !z_host) return CSL_INVALID_ARG;
   if (!(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
   const size_t bytes = sizeof(double2) * P->M;
+  NvtxRange r("csl_solve_host");
   CSL_TRY(cudaMemcpyAsync(P->io, f_host, bytes, cudaMemcpyHostToDevice, P->stream));
-  csl_status s = solve_impl(P, P->io, tol, maxit, P->beta);
+  if (P->warm) CSL_TRY(cudaMemcpyAsync(P->x0, z_host, bytes, cudaMemcpyHostToDevice, P->stream));
+  csl_status s = solve_impl(P, P->io, tol, maxit, P->beta, P->x0);
   if (s != CSL_OK) return s;
   CSL_TRY(copy_out(P, P->io, P->stream));  // f is no longer needed
   CSL_TRY(cudaMemcpyAsync(z_host, P->io, bytes, cudaMemcpyDeviceToHost, P->stream));
   csl_status st = CSL_OK;
   s = read_info(P, info, &st);
   return s != CSL_OK ? s : st;
+}
+
+csl_status csl_solve_history(csl_plan* P, double* out_host, int cap, int* count) {
+  if (!P || !out_host || !count || cap < 0) return CSL_INVALID_ARG;
+  *count = 0;
+  if (!P->hist) return CSL_INVALID_ARG;
+  DevState h;
+  CSL_TRY(cudaMemcpyAsync(&h, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->stream));
+  CSL_TRY(cudaStreamSynchronize(P->stream));
+  int n = h.iter < P->hist_cap ? h.iter : P->hist_cap;
+  if (n > cap) n = cap;
+  if (n > 0) {
+    CSL_TRY(cudaMemcpyAsync(out_host, P->hist, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream));
+    CSL_TRY(cudaStreamSynchronize(P->stream));
+  }
+  *count = n;
+  return CSL_OK;
 }
 
 csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* const grad_faces[3]) {
@@ -1259,6 +1463,9 @@ csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* 
   CSL_TRY(cudaGetLastError());
   return CSL_OK;
 }
+
+// launches per timed group of csl_time_kernels
+constexpr int kTimeGroup = 4;
 
 csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* names[8], int* count) {
   if (!P || !ms || !names || !count || reps < 1) return CSL_INVALID_ARG;
@@ -1284,7 +1491,7 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   static const char* n3[7] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
                               "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
   static const char* p3split = "k_row<LOAD_T,STORE_Z>";
-  const int st3 = P->split_update ? STORE_Z : STORE_Z_UPDATE;
+  const int st3 = P->split_update ? STORE_Z : update_store(P);
   int k = 0;
   for (k = 0; k < nk && err == cudaSuccess; ++k) {
     double tot = 0.0;
@@ -1292,11 +1499,14 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
       err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
       if (err == cudaSuccess) err = cudaEventRecord(e0, P->stream);
       if (err != cudaSuccess) break;
-      const int par = r & 1;
+      // a group of kTimeGroup back-to-back launches between the events, so
+      // that the host's submission latency is not counted in the duration
+      for (int g = 0; g < kTimeGroup && err == cudaSuccess; ++g) {
+      const int par = g & 1;
       if (k == 0) {
         err = fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
       } else if (k == 1) {
-        err = fp32 ? run_row<float>(P, LOAD_LANCZOS, STORE_T, p1_args<float>(P, par), P->stream)
+        err = fp32 ? run_row<float>(P, lanczos_load(P), STORE_T, p1_args<float>(P, par), P->stream)
                    : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
       } else if (k == nkb) {
         err = fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
@@ -1325,11 +1535,12 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
           err = launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
         }
       }
+      }
       if (err == cudaSuccess) err = cudaEventRecord(e1, P->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float t = 0.f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
-      tot += t;
+      tot += t / kTimeGroup;
     }
     ms[k] = tot / reps;
     names[k] = (P->split_update && k == nkb - 1) ? p3split : P->dim == 2 ? n2[k] : n3[k];
@@ -1523,7 +1734,7 @@ cudaError_t build_group_args(csl_batch* B, BatchGroup& G) {
     ia.sqrt_pmin = P->sqrt_pmin;
     ia.sqrt_pmax = P->sqrt_pmax;
     ia.beta = P->beta;
-    ia.vpair = sizeof(T) == 4 ? 1 : 0;
+    ia.vpair = P->vpair;
     G.h_ing[i] = ia;
   }
   if (e == cudaSuccess) e = upload_array(B, &G.d_mid, mid);
@@ -1562,16 +1773,17 @@ cudaError_t group_iteration(csl_batch* B, BatchGroup& G, int par, cudaStream_t s
   memset(&sd, 0, sizeof(sd));
   const StencilArgs* sb = (const StencilArgs*)G.d_sten[par];
   const size_t smem = (sizeof(TZ) == 8 && G.ff) ? ff_stencil_smem(P->dim) : 0;
-  cudaError_t e = launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, G.ff != 0), P->sten_blocks * ns, 256, smem, s,
+  cudaError_t e = launch_k(P->use_pdl != 0, stencil_fn<TZ>(P->dim, G.ff != 0, P->vpair != 0), P->sten_blocks * ns, 256,
+                           smem, s,
                            sd, sb, P->sten_blocks);
   RowArgs<T> rd;
   memset(&rd, 0, sizeof(rd));
   if (e == cudaSuccess)
-    e = launch_row<T>(P->row.N, P->row.wide, LOAD_LANCZOS, STORE_T, rd, P->row.L, s,
+    e = launch_row<T>(P->row.N, P->row.wide, lanczos_load(P), STORE_T, rd, P->row.L, s,
                       (const RowArgs<T>*)G.d_p1[par], ns);
   if (e == cudaSuccess) e = group_mid_chain<T>(B, G, s, G.d_mid);
   if (e == cudaSuccess)
-    e = launch_row<T>(P->row.N, P->row.wide, LOAD_T, STORE_Z_UPDATE, rd, P->row.L, s,
+    e = launch_row<T>(P->row.N, P->row.wide, LOAD_T, update_store(P), rd, P->row.L, s,
                       (const RowArgs<T>*)G.d_p3[par], ns);
   return e;
 }
@@ -1687,7 +1899,7 @@ csl_status batch_solve_T(csl_batch* B, const double* const* f, double* const* z,
   CSL_TRY(cudaMemcpyAsync(B->d_dst, dst.data(), sizeof(void*) * B->nsys, cudaMemcpyHostToDevice, s));
   CSL_TRY(cudaMemcpyAsync(B->d_count, cnt.data(), sizeof(long) * B->nsys, cudaMemcpyHostToDevice, s));
   dim3 grid((unsigned)((B->maxM + 255) / 256 < 256 ? (B->maxM + 255) / 256 : 256), (unsigned)B->nsys);
-  k_batch_copy<<<grid, 256, 0, s>>>(B->d_src, B->d_dst, B->d_count, sizeof(T) == 4 ? 1 : 0);
+  k_batch_copy<<<grid, 256, 0, s>>>(B->d_src, B->d_dst, B->d_count, B->plans[0]->vpair);
   CSL_TRY(cudaGetLastError());
   std::vector<DevState> h(B->nsys);
   CSL_TRY(cudaMemcpyAsync(h.data(), B->states, sizeof(DevState) * B->nsys, cudaMemcpyDeviceToHost, s));
@@ -1722,6 +1934,8 @@ csl_status csl_batch_create(csl_batch** out, int nsys, const csl_system_desc* sy
   if (opt) o = *opt;
   for (int i = 0; i < nsys; ++i)
     if (sys[i].dim != sys[0].dim) return CSL_INVALID_ARG;
+  if (o.warm_start || o.history) return CSL_INVALID_ARG;  // single plans only
+  NvtxRange nv("csl_batch_create");
   csl_batch* B = new (std::nothrow) csl_batch();
   if (!B) return CSL_OUT_OF_MEMORY;
   B->nsys = nsys;
@@ -1795,6 +2009,7 @@ csl_status csl_batch_solve(csl_batch* B, const double* const* f, double* const* 
   if (!B || !f || !z || !(tol > 0.0) || maxit < 1) return CSL_INVALID_ARG;
   for (int i = 0; i < B->nsys; ++i)
     if (!f[i] || !z[i]) return CSL_INVALID_ARG;
+  NvtxRange nv("csl_batch_solve");
   return B->precision != CSL_PREC_FP64 ? batch_solve_T<float>(B, f, z, tol, maxit, infos)
                                        : batch_solve_T<double>(B, f, z, tol, maxit, infos);
 }

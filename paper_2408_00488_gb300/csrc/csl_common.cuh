@@ -94,12 +94,15 @@ struct DevState {
   double eta_x;   // |eta| belonging to the current iterate x
   double beta;    // coupling coefficient of this solve (beta, or -beta for the adjoint)
   double sqrt_pmin, sqrt_pmax;  // sqrt of extreme eigenvalues of one block of P
+  double r0norm;  // ||b - A x_0||_2 of the start vector (= bnorm for x_0 = 0)
+  double* hist;   // optional: |eta_j| / gamma_1 of every iteration j (hist_cap entries), or null
+  int hist_cap;
   int iter;       // completed iterations = index of the current iterate x
   int maxit, done, status, check, lucky, checks, calibrated, loops;
   unsigned int tickets[4];
 };
 
-enum { TICKET_STENCIL = 0, TICKET_MID = 1, TICKET_INGEST = 2, TICKET_AUX = 3 };
+enum { TICKET_STENCIL = 0, TICKET_MID = 1, TICKET_INGEST = 2, TICKET_AUX = 3 };  // TICKET_AUX: warm start
 
 // status codes mirrored from csl.h
 enum {

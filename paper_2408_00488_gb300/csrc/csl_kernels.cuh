@@ -197,18 +197,20 @@ __device__ __forceinline__ float2 d_to_ff(double d) {
 // Lanczos vectors v (and u'): FP64 in the FP64 form; in the FP32 forms each
 // component is a float pair (re.hi, re.lo, im.hi, im.lo) in the same 16 bytes
 // per point, so that the stencil and the Lanczos step run in pair arithmetic.
-template <typename TZ>
+// VP: the vectors are stored as float pairs (CSL_PREC_FP32 and the split-BF16
+// forms); otherwise as FP64 (CSL_PREC_FP64 and CSL_PREC_FP32_PRECOND).
+template <bool VP>
 __device__ __forceinline__ double2 v_load(const double2* v, long p) {
-  if constexpr (sizeof(TZ) == 16) {
+  if constexpr (!VP) {
     return v[p];
   } else {
     const float4 q = ((const float4*)v)[p];
     return make_double2(f2d_exact(q.x) + f2d_exact(q.y), f2d_exact(q.z) + f2d_exact(q.w));
   }
 }
-template <typename TZ>
+template <bool VP>
 __device__ __forceinline__ void v_store(double2* v, long p, double2 val) {
-  if constexpr (sizeof(TZ) == 16) {
+  if constexpr (!VP) {
     v[p] = val;
   } else {
     const float2 a = d_to_ff(val.x), b = d_to_ff(val.y);
@@ -325,7 +327,7 @@ struct StripWindow {
 // so that the loads of step m+1 are in flight while step m computes: z at
 // m+1 (the window's next value), the edge lanes' x-neighbours, in 3D the
 // y-neighbours, the diagonal, the faces and v_{j-1}.
-template <int DIM, typename TZ>
+template <int DIM, typename TZ, bool VP>
 struct StepOperands {
   TZ zn1, zl, zr, ys, yn;
   double d, cw, ce, cs, cn, cd, cu;
@@ -360,7 +362,7 @@ struct StepOperands {
       ce = a.cx[rx + 1];
       cs = a.cy[ry];
       cn = a.cy[ry + nx];
-      vo = v_load<TZ>(a.vold, p);
+      vo = v_load<VP>(a.vold, p);
     }
   }
 };
@@ -416,9 +418,10 @@ __host__ __device__ constexpr int ff_stencil_smem(int dim) {
 // the large cancelling terms c_e z_p of the direct form never appear), and
 // add the beta block term, delta and u' = A ẑ - lanc v_{j-1} (v held as float
 // pairs) in pairs too: no FP64 arithmetic per point.
-template <int DIM, typename TZ, bool FF>
+template <int DIM, typename TZ, bool FF, bool VP>
 __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
-  static_assert(!FF || sizeof(TZ) == 8, "the float-pair stencil reads an FP32 z");
+  static_assert(!FF || (sizeof(TZ) == 8 && VP), "the float-pair stencil reads an FP32 z and pair vectors");
+  static_assert(!VP || sizeof(TZ) == 8, "pair vectors go with an FP32 z");
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
   const int bid = batch ? (int)blockIdx.x - sys * bps : (int)blockIdx.x;
   const int nblk = batch ? bps : (int)gridDim.x;
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
       const double2 zero = make_double2(0.0, 0.0);
       double2 zm = (vx && m0 > 0) ? to_d2(z[base + (long)(m0 - 1) * mstride]) : zero;
       double2 zc = vx ? to_d2(z[base + (long)m0 * mstride]) : zero;
-      StepOperands<DIM, TZ> cur, nxt;
+      StepOperands<DIM, TZ, VP> cur, nxt;
       cur.load(z, a, base + (long)m0 * mstride, mstride, m0, nm, x, yfix, vx, lane);
       for (int m = m0; m < m1; ++m) {
         const long p = base + (long)m * mstride;
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
           }
           const double2 Az = block_A(make_double2(ax, ay), zc, beta);
           acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
-          v_store<TZ>(a.vold, p, make_double2(fma(-lanc, cur.vo.x, Az.x), fma(-lanc, cur.vo.y, Az.y)));
+          v_store<VP>(a.vold, p, make_double2(fma(-lanc, cur.vo.x, Az.x), fma(-lanc, cur.vo.y, Az.y)));
         }
         zm = zc;
         zc = zp;
@@ -615,8 +618,8 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
       }
       continue;
     }
-    // x is FP64 in the FP64 form and float pairs in the FP32 forms
-    typedef typename std::conditional<sizeof(TZ) == 8, float4, double2>::type TX;
+    // x is float pairs in the pair-vector forms, else FP64
+    typedef typename std::conditional<VP, float4, double2>::type TX;
     const TX* xs = (const TX*)a.x;
     StripWindow<DIM, TZ> wz;
     StripWindow<DIM, TX> wx;
@@ -631,8 +634,8 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
         const double2 zc = wz.zc;
         const double2 Az = block_A(t, zc, beta);
         acc[0] = fma(Az.x, zc.x, fma(Az.y, zc.y, acc[0]));
-        const double2 vo = v_load<TZ>(a.vold, p);
-        v_store<TZ>(a.vold, p, make_double2(fma(-lanc, vo.x, Az.x), fma(-lanc, vo.y, Az.y)));
+        const double2 vo = v_load<VP>(a.vold, p);
+        v_store<VP>(a.vold, p, make_double2(fma(-lanc, vo.x, Az.x), fma(-lanc, vo.y, Az.y)));
         if (check) {
           const double2 Ax = block_A(tx, wx.zc, beta);
           const double2 bb = a.b[p];
@@ -740,6 +743,7 @@ __device__ inline void givens_step(DevState* st, double g2) {
   // stopping-test schedule for x_iter (evaluated by the next stencil pass)
   const double e = fabs(st->eta);
   st->eta_x = e;
+  if (st->hist && st->iter <= st->hist_cap) st->hist[st->iter - 1] = e / st->gam1;
   const double target = st->tol * st->bnorm;
   const double pred = st->rho * e;  // predicted ||b - A x||_2
   int chk = 0;
@@ -794,13 +798,13 @@ __device__ __forceinline__ void ff_update(float z, float2 wp, float2 wq, float2 
   xn = ff_two_sum(xa.h, xa.l);
 }
 
-template <typename TZ>
+template <typename TZ, bool VP>
 __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
   if (a.st->done) return;
   const double wb = a.st->w_b, wc = a.st->w_c, xc = a.st->x_coef;
   const TZ* z = (const TZ*)a.z;
   constexpr int U = kUpdateUnroll;
-  if constexpr (sizeof(TZ) == 8) {  // FP32 forms: w and x as float pairs
+  if constexpr (VP) {  // pair-vector forms: w and x as float pairs
     const float2 wb2 = d_to_ff(wb), wc2 = d_to_ff(wc), xc2 = d_to_ff(xc);
     const float4* wq4 = (const float4*)a.wcur;
     float4* wp4 = (float4*)a.wprev;
@@ -906,6 +910,7 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const Inge
   if (threadIdx.x != 0) return;
   DevState* st = a.st;
   st->bnorm = sqrt(tot[0]);
+  st->r0norm = st->bnorm;
   st->tol = a.tol;
   st->maxit = a.maxit;
   st->beta = a.beta;
@@ -927,10 +932,75 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const Inge
   st->status = ST_OK;
   st->relres = 1.0;
   st->done = 0;
-  if (!(st->bnorm > 0.0)) {  // f = 0: z = 0 is exact (or f is not finite)
+  if (st->bnorm == 0.0) {  // f = 0: z = 0 is exact
     st->done = 1;
     st->relres = 0.0;
-    st->status = (st->bnorm == 0.0) ? ST_OK : ST_BREAKDOWN;
+    st->status = ST_OK;
+  } else if (!(st->bnorm < INFINITY)) {  // f holds a NaN or an infinity
+    st->done = 1;
+    st->relres = __longlong_as_double(0x7ff8000000000000ll);
+    st->status = ST_BREAKDOWN;
+  }
+}
+
+// Warm start: with the initial guess x_0, MINRES runs on the correction
+// A d = b - A x_0 from d = 0 (x = x_0 + d), so the block right-hand side and
+// v_1 become r_0 = b - A x_0 (Eq. 2's operator in FP64); ||r_0|| calibrates
+// the residual estimate, while the stopping test stays relative to ||b||.
+// x_0 already meeting the tolerance ends the solve at once with x = x_0.
+struct WarmArgs {
+  Grid g;
+  const double2* x0;  // block pairs (Re, Im) of the caller's initial guess
+  double2 *b, *v0;
+  const double *cx, *cy, *cz, *dg;
+  DevState* st;
+  double* partials;
+  int vpair;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_warm_start(WarmArgs a) {
+  DevState* st = a.st;
+  if (st->done) return;  // f = 0 or not finite: decided by the ingest
+  const double beta = st->beta;
+  double acc[1] = {0.0};
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < a.g.M; p += (long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    point_coords(p, a.g, ix, iy, iz);
+    double2 xc;
+    const double2 Ax = block_A(stencil_KA<DIM, double2>(a.x0, a.cx, a.cy, a.cz, a.dg, a.g, p, ix, iy, iz, xc), xc, beta);
+    const double2 bb = a.b[p];
+    const double2 r = make_double2(bb.x - Ax.x, bb.y - Ax.y);
+    a.b[p] = r;
+    if (a.vpair) {
+      const float2 re = d_to_ff(r.x), im = d_to_ff(r.y);
+      ((float4*)a.v0)[p] = make_float4(re.x, re.y, im.x, im.y);
+    } else {
+      a.v0[p] = r;
+    }
+    acc[0] = fma(r.x, r.x, fma(r.y, r.y, acc[0]));
+  }
+  double tot[1];
+  if (!grid_sum_last_block<1>(acc, a.partials, &st->tickets[TICKET_AUX], tot, blockIdx.x, gridDim.x)) return;
+  if (threadIdx.x != 0) return;
+  st->r0norm = sqrt(tot[0]);
+  st->relres = st->r0norm / st->bnorm;
+  if (!(st->r0norm < INFINITY)) {
+    st->done = 1;
+    st->status = ST_BREAKDOWN;
+  } else if (st->r0norm <= st->tol * st->bnorm) {
+    st->done = 1;
+    st->status = ST_OK;
+  }
+}
+
+// egress with a warm start: z = x_0 + d (d as float pairs or FP64)
+static __global__ void k_x_out_add(const double2* __restrict__ d, int pairs, const double2* __restrict__ x0,
+                                   double2* __restrict__ out, long M) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (long)gridDim.x * blockDim.x) {
+    const double2 dd = pairs ? to_d2(((const float4*)d)[p]) : d[p];
+    const double2 x = x0[p];
+    out[p] = make_double2(x.x + dd.x, x.y + dd.y);
   }
 }
 

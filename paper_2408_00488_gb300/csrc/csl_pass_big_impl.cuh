@@ -12,6 +12,20 @@ cudaError_t launch_row_big_n(int load, int store, const RowArgs<T>& a, const Pas
                              const RowArgs<T>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
   const int bps = L.blocks;
+  if constexpr (sizeof(T) == 8) {  // the FP64 form's vectors are FP64 in the plain modes
+    if (load == LOAD_LANCZOS_V64) load = LOAD_LANCZOS;
+    if (store == STORE_Z_UPDATE_V64) store = STORE_Z_UPDATE;
+  }
+  if constexpr (sizeof(T) == 4) {  // FP32 transform, FP64 vectors
+    if (load == LOAD_LANCZOS_V64 && store == STORE_T) {
+      k_row<T, N, 3, LOAD_LANCZOS_V64, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+      return cudaGetLastError();
+    }
+    if (load == LOAD_T && store == STORE_Z_UPDATE_V64) {
+      k_row<T, N, 3, LOAD_T, STORE_Z_UPDATE_V64><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
+      return cudaGetLastError();
+    }
+  }
   if (load == LOAD_V && store == STORE_T)
     k_row<T, N, 3, LOAD_V, STORE_T><<<grid, L.threads, L.smem, s>>>(a, batch, bps);
   else if (load == LOAD_LANCZOS && store == STORE_T)
@@ -81,7 +95,11 @@ cudaError_t set_pass_attrs_big() {
   SETA((k_row<T, NN, 3, LOAD_T, STORE_Z_UPDATE>)) \
   SETA((k_row<T, NN, 3, LOAD_T, STORE_D>))        \
   SETA((k_strided<T, NN, 3, true>))               \
-  SETA((k_strided<T, NN, 3, false>))
+  SETA((k_strided<T, NN, 3, false>))             \
+  if constexpr (sizeof(T) == 4) {                 \
+    SETA((k_row<T, NN, 3, LOAD_LANCZOS_V64, STORE_T>)) \
+    SETA((k_row<T, NN, 3, LOAD_T, STORE_Z_UPDATE_V64>)) \
+  }
   CSL_FOR_EACH_BIG_N(CASE)
 #undef CASE
 #undef SETA

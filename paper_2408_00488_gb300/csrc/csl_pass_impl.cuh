@@ -11,6 +11,17 @@ cudaError_t launch_row_n(int load, int store, const RowArgs<T>& a, const PassLau
                          const RowArgs<T>* batch, int nsys) {
   const int grid = batch ? L.blocks * nsys : L.blocks;
   const int bps = L.blocks;
+  if constexpr (sizeof(T) == 4) {  // FP32 transform, FP64 vectors
+    if (load == LOAD_LANCZOS_V64 && store == STORE_T)
+      return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_LANCZOS_V64, STORE_T>, grid, L.threads, L.smem, s, a, batch,
+                      bps);
+    if (load == LOAD_T && store == STORE_Z_UPDATE_V64)
+      return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_T, STORE_Z_UPDATE_V64>, grid, L.threads, L.smem, s, a, batch,
+                      bps);
+  } else {  // the FP64 form's vectors are FP64 in the plain modes
+    if (load == LOAD_LANCZOS_V64) load = LOAD_LANCZOS;
+    if (store == STORE_Z_UPDATE_V64) store = STORE_Z_UPDATE;
+  }
   if (load == LOAD_V && store == STORE_T)
     return launch_k(L.pdl != 0, k_row<T, N, W, LOAD_V, STORE_T>, grid, L.threads, L.smem, s, a, batch, bps);
   else if (load == LOAD_LANCZOS && store == STORE_T)
@@ -83,7 +94,11 @@ cudaError_t set_pass_attrs() {
   SETA((k_row<T, NN, W, LOAD_T, STORE_Z_UPDATE>))      \
   SETA((k_row<T, NN, W, LOAD_T, STORE_D>))             \
   SETA((k_strided<T, NN, W, true>))                    \
-  SETA((k_strided<T, NN, W, false>))
+  SETA((k_strided<T, NN, W, false>))                   \
+  if constexpr (sizeof(T) == 4) {                      \
+    SETA((k_row<T, NN, W, LOAD_LANCZOS_V64, STORE_T>)) \
+    SETA((k_row<T, NN, W, LOAD_T, STORE_Z_UPDATE_V64>)) \
+  }
 #define CASE(NN) VARIANT(NN, 0)
   CSL_FOR_EACH_N(CASE)
 #undef CASE

@@ -25,8 +25,11 @@
 
 namespace csl {
 
-enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2 };
-enum { STORE_T = 0, STORE_D = 1, STORE_Z = 2, STORE_Z_UPDATE = 3 };
+// LOAD_LANCZOS_V64 / STORE_Z_UPDATE_V64: the FP32 transform with the MINRES
+// vectors v, w and x in FP64 (CSL_PREC_FP32_PRECOND); with T = float the plain
+// LOAD_LANCZOS / STORE_Z_UPDATE hold them as float pairs, with T = double in FP64
+enum { LOAD_V = 0, LOAD_T = 1, LOAD_LANCZOS = 2, LOAD_LANCZOS_V64 = 3 };
+enum { STORE_T = 0, STORE_D = 1, STORE_Z = 2, STORE_Z_UPDATE = 3, STORE_Z_UPDATE_V64 = 4 };
 
 template <typename T>
 struct RowArgs {
@@ -98,8 +101,13 @@ __host__ __device__ constexpr int pass_max_threads() {
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
-template <typename T, int N, int WIDE, int LOAD, int STORE>
+template <typename T, int N, int WIDE, int LOAD_MODE, int STORE_MODE>
 __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
+  // the V64 modes are the Lanczos / update modes with FP64 vectors
+  constexpr int LOAD = LOAD_MODE == LOAD_LANCZOS_V64 ? LOAD_LANCZOS : LOAD_MODE;
+  constexpr int STORE = STORE_MODE == STORE_Z_UPDATE_V64 ? STORE_Z_UPDATE : STORE_MODE;
+  // v, w and x stored as float pairs
+  constexpr bool pairs = sizeof(T) == 4 && LOAD_MODE != LOAD_LANCZOS_V64 && STORE_MODE != STORE_Z_UPDATE_V64;
   typedef typename C2<T>::t c_t;
   typedef LineDst<T, N, WIDE> D;
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     wb = a.st->w_b;
     wc = a.st->w_c;
     xc = a.st->x_coef;
-    if (sizeof(T) == 4) {
+    if (pairs) {
       wb2 = d_to_ff(wb);
       wc2 = d_to_ff(wc);
       xc2 = d_to_ff(xc);
@@ -160,8 +168,8 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     // global loads in batches of UB elements per lane, all issued before use
 #pragma unroll
     for (int i0 = 0; i0 < NL; i0 += UB) {
-      if (LOAD == LOAD_LANCZOS && sizeof(T) == 4) {
-        // FP32 forms: u' and v_j are float pairs (re.hi, re.lo, im.hi, im.lo);
+      if constexpr (LOAD == LOAD_LANCZOS && pairs) {
+        // pair-vector forms: u' and v_j are float pairs (re.hi, re.lo, im.hi, im.lo);
         // v_{j+1} = u' - (delta/gamma) v_j in pair arithmetic, stored
         // renormalised, its hi parts (= RN of the pair) feed the transform
         float4 u[UB], vc[UB];
@@ -256,13 +264,13 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
               const long p = base + j;
               const c_t F = line[D::out_pos(j + 1)];
               a.zout[p] = mkc<T>(F.x * zs, F.y * zs);
-              if constexpr (sizeof(T) == 4) {  // FP32 forms: w and x as float pairs (see k_update)
+              if constexpr (pairs) {  // pair-vector forms: w and x as float pairs (see k_update)
                 const float4 q = *(const float4*)&wp[k], r = *(const float4*)&wq[k], o = *(const float4*)&xo[k];
                 ff2 wr, xr, wi, xi;
-                ff_update(zo[k].x, make_float2(q.x, q.y), make_float2(r.x, r.y), make_float2(o.x, o.y), wb2, wc2, xc2,
-                          wr, xr);
-                ff_update(zo[k].y, make_float2(q.z, q.w), make_float2(r.z, r.w), make_float2(o.z, o.w), wb2, wc2, xc2,
-                          wi, xi);
+                ff_update(zo[k].x, make_float2(q.x, q.y), make_float2(r.x, r.y), make_float2(o.x, o.y), wb2, wc2,
+                          xc2, wr, xr);
+                ff_update(zo[k].y, make_float2(q.z, q.w), make_float2(r.z, r.w), make_float2(o.z, o.w), wb2, wc2,
+                          xc2, wi, xi);
                 ((float4*)a.wprev)[p] = make_float4(wr.h, wr.l, wi.h, wi.l);
                 ((float4*)a.x)[p] = make_float4(xr.h, xr.l, xi.h, xi.l);
                 continue;
@@ -321,7 +329,7 @@ __device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, 
     st->gam_old = 1.0;
     st->eta = st->gam;
     st->eta_x = st->gam;
-    st->rho = st->bnorm / st->gam;  // exact at x_0 = 0
+    st->rho = st->r0norm / st->gam;  // exact at the start vector
     return;
   }
   givens_step(st, tot[0]);

@@ -1,9 +1,9 @@
 // csl_precondition_static: P^{-1} v (the preconditioner application of
 // csl_precondition) for callers that cannot allocate device memory -- for
-// example code running inside a memory-pool-managed runtime, a fixed-budget
-// embedded service, or a stream-capture context where cudaMalloc is not
-// allowed.  It allocates nothing: all scratch lives in the file-scope
-// __device__ arrays below, sized for grids of at most kStaticMaxPoints points.
+// example code running inside a runtime whose memory pool owns all device
+// memory, or a fixed-budget embedded service.  It allocates nothing: all
+// scratch lives in the file-scope __device__ arrays below, sized for grids
+// of at most kStaticMaxPoints points.
 //
 // Every call on a device shares these arrays (every GPU that loads the
 // library holds them until the process exits), so calls that overlap on the
@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "../../include/csl.h"
 #include "csl_passes.cuh"
@@ -181,9 +182,63 @@ PassLaunch static_launch(int N, long nlines_or_tiles_per_cta_unit, bool strided,
   return L;
 }
 
+// Host-side check of the per-mode scales before anything is launched (the
+// call is asynchronous, so the device cannot report a status): every mode's
+// q = (gamma mu + alpha)^2 + beta^2 over the grid's modes, mu the sum of the
+// per-axis eigenvalues mu_k = (4/h^2) sin^2(k pi / (2N)).  Returns
+// CSL_SINGULAR_PRECOND when some q is zero to within rounding (only possible
+// for beta = 0, as for csl_plan_create), and for FP32 the power of two sigma
+// by which gamma, alpha, beta and cnorm are prescaled (as the plan does), or
+// CSL_INVALID_ARG when the scales cnorm / sqrt(q) leave the FP32 range.
+csl_status static_check_scales(int dim, const int n[3], double gamma, double alpha, double beta, double cnorm,
+                               bool fp32, double* sigma) {
+  std::vector<double> mu[3];
+  for (int d = 0; d < dim; ++d) {
+    const int N = n[d] + 1;
+    const double h = 1.0 / (double)N;
+    mu[d].resize(n[d]);
+    for (int k = 1; k <= n[d]; ++k) {
+      const double sn = sin(M_PI * (double)k / (2.0 * N));
+      mu[d][k - 1] = 4.0 / (h * h) * sn * sn;
+    }
+  }
+  double qmin = INFINITY, qmax = 0.0;
+  bool zero = false;
+  const int nz = dim == 3 ? n[2] : 1;
+  for (int iz = 0; iz < nz; ++iz)
+    for (int iy = 0; iy < n[1]; ++iy)
+      for (int ix = 0; ix < n[0]; ++ix) {
+        const double m = mu[0][ix] + mu[1][iy] + (dim == 3 ? mu[2][iz] : 0.0);
+        const double e = gamma * m + alpha;
+        // |e| at the level of the rounding of gamma mu + alpha counts as zero
+        if (beta == 0.0 && fabs(e) <= 16.0 * 2.2204460492503131e-16 * (fabs(gamma * m) + fabs(alpha))) zero = true;
+        const double q = e * e + beta * beta;
+        qmin = q < qmin ? q : qmin;
+        qmax = q > qmax ? q : qmax;
+      }
+  if (zero || !(qmin > 0.0)) {
+    csl_internal_set_error("csl_precondition_static: (gamma mu + alpha)^2 + beta^2 = 0 for some mode (singular P)");
+    return CSL_SINGULAR_PRECOND;
+  }
+  *sigma = 1.0;
+  if (fp32) {
+    // the plan's FP32 rule: |e + i beta| is brought to at most 2^40 when it
+    // leaves [2^-40, 2^60]; the scales themselves must be normal floats
+    const double mmin = sqrt(qmin), mmax = sqrt(qmax);
+    if (mmax > ldexp(1.0, 60) || mmin < ldexp(1.0, -40)) *sigma = ldexp(1.0, 40 - (int)ceil(log2(mmax)));
+    const double smin = cnorm / mmax, smax = cnorm / mmin;
+    if (!(smin >= ldexp(1.0, -120)) || !(smax <= ldexp(1.0, 120)) || !(mmin * *sigma >= ldexp(1.0, -60))) {
+      csl_internal_set_error(
+          "csl_precondition_static: the per-mode scales of P^-1 lie outside the FP32 range; use CSL_PREC_FP64");
+      return CSL_INVALID_ARG;
+    }
+  }
+  return CSL_OK;
+}
+
 template <typename T>
-cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, double beta, const double2* v,
-                       double2* out, cudaStream_t s, const StaticPtrs& P) {
+cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, double beta, double sigma,
+                       const double2* v, double2* out, cudaStream_t s, const StaticPtrs& P) {
   typedef typename C2<T>::t c_t;
   const long M = (long)n[0] * n[1] * n[2];
   double cnorm = 1.0;
@@ -237,10 +292,11 @@ cudaError_t run_static(int dim, const int n[3], double gamma, double alpha, doub
         a.mu_col = (const T*)ax[0].mu_f;
         a.mu_outer = axis == 2 ? (const T*)ax[1].mu_f : nullptr;
       }
-      a.gamma = (T)gamma;
-      a.alpha = (T)alpha;
-      a.beta2 = (T)(beta * beta);
-      a.cnorm = (T)cnorm;
+      // FP32: gamma, alpha, beta and cnorm times sigma (s_k unchanged, e^2 + beta^2 in range)
+      a.gamma = (T)(gamma * sigma);
+      a.alpha = (T)(alpha * sigma);
+      a.beta2 = (T)((beta * sigma) * (beta * sigma));
+      a.cnorm = (T)(cnorm * sigma);
     }
     const PassLaunch L = static_launch<T>(nn + 1, 0, true, nx, nouter);
     return launch_strided<T>(nn + 1, pass_has_wide(nn + 1) ? 1 : 0, mid, a, L, s);
@@ -284,6 +340,10 @@ extern "C" csl_status csl_precondition_static(int dim, const int64_t n[3], doubl
     csl_internal_set_error(msg);
     return CSL_UNSUPPORTED_SIZE;
   }
+  double cnorm = 1.0, sigma = 1.0;
+  for (int d = 0; d < dim; ++d) cnorm *= 2.0 / (double)(nn[d] + 1);
+  const csl_status chk = static_check_scales(dim, nn, gamma, alpha, beta, cnorm, precision == CSL_PREC_FP32, &sigma);
+  if (chk != CSL_OK) return chk;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -296,9 +356,9 @@ extern "C" csl_status csl_precondition_static(int dim, const int64_t n[3], doubl
     return CSL_CUDA_ERROR;
   }
   e = (precision == CSL_PREC_FP32)
-          ? run_static<float>(dim, nn, gamma, alpha, beta, (const double2*)v, (double2*)out, (cudaStream_t)stream,
-                              g_ptrs[dev])
-          : run_static<double>(dim, nn, gamma, alpha, beta, (const double2*)v, (double2*)out,
+          ? run_static<float>(dim, nn, gamma, alpha, beta, sigma, (const double2*)v, (double2*)out,
+                              (cudaStream_t)stream, g_ptrs[dev])
+          : run_static<double>(dim, nn, gamma, alpha, beta, 1.0, (const double2*)v, (double2*)out,
                                (cudaStream_t)stream, g_ptrs[dev]);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();

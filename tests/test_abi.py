@@ -133,4 +133,23 @@ def test_options_init_enables_the_fast_paths(csl):
     o = csl._binding.PlanOptions()
     assert csl.lib.csl_plan_options_init(ctypes.byref(o)) == 0
     assert o.programmatic_launch == 1 and o.float_pair_stencil == 1
+    assert o.update_mode == 0 and o.body_iters == 0 and o.warm_start == 0 and o.history == 0
     assert all(r == 0 for r in o.reserved)
+
+
+def test_tune_cache_files_checked_on_the_host(csl, tmp_path):
+    """The tuner's cache file is written and read on the host: a malformed
+    file loads nothing, and a missing one is an argument error."""
+    b = csl._binding
+    good = tmp_path / "tc.txt"
+    assert csl.lib.csl_tune_cache_save(str(good).encode()) == b.OK
+    assert open(good).read().splitlines()[0] == "csl-tune-cache 1"
+    assert csl.lib.csl_tune_cache_load(str(good).encode()) == b.OK
+    for body in ("not a cache\n", "csl-tune-cache 1\n4 2 1000 7 1 0 4\n", "csl-tune-cache 1\n4 2 1024 7 1 5 4\n",
+                 "csl-tune-cache 1\n4 2 1024 7 1 0 3\n", "csl-tune-cache 1\n4 2 1024\n"):
+        bad = tmp_path / "bad.txt"
+        bad.write_text(body)
+        assert csl.lib.csl_tune_cache_load(str(bad).encode()) == b.INVALID_ARG, body
+    assert csl.lib.csl_tune_cache_load(str(tmp_path / "missing.txt").encode()) == b.INVALID_ARG
+    assert csl.lib.csl_tune_cache_load(None) == b.INVALID_ARG
+    assert csl.lib.csl_solve_history(None, None, 0, None) == b.INVALID_ARG

@@ -52,7 +52,7 @@ def test_apply_parity(csl, dim, n, coef):
 
 
 @pytest.mark.parametrize("dim,n,coef", GRIDS + [(2, 1023, W.coef_c1), (3, 127, W.coef_c2)])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("fp32_precond", 2e-5)])
 def test_precondition_parity(csl, dim, n, coef, precision, tol):
     faces = W.sample_faces(dim, n, coef)
     lam = 1 + 10j
@@ -86,7 +86,7 @@ def _solve_and_compare(csl, faces, lam, f, precision, tol=1e-8, maxit=600, oracl
     return info, oinfo, res, err
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_precond"])
 def test_solve_config0(csl, precision):
     s = W.config0()
     info, oinfo, res, err = _solve_and_compare(csl, s.faces, s.lam, s.f, precision)
@@ -97,7 +97,7 @@ def test_solve_config0(csl, precision):
     assert err <= 1e-7, err
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_precond"])
 @pytest.mark.parametrize("dim,n,coef,lam", [(3, 15, W.coef_c2, -5 + 50j), (2, 31, W.coef_c1, 100j),
                                             (3, 7, W.coef_c0 if False else W.coef_c2, 1 + 10j)])
 def test_solve_small_grids(csl, precision, dim, n, coef, lam):
@@ -225,3 +225,50 @@ def test_coef_grad_3d_parity(csl):
         gg = plan.coef_grad(dev(z), dev(y))
     for a, b in zip(gg, gref):
         assert a.shape == b.shape and rel(host(a), b) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gamma_uses_every_axis(csl, dim):
+    # Eq. 4 with a_min only among the y- (or z-) faces and a_max only among the
+    # x- (or y-) faces: gamma = sqrt(0.25 * 9) = 1.5, and P^{-1} follows it
+    n = 7
+    shape = (n,) * dim
+    faces = []
+    for a in range(dim):
+        s = list(shape)
+        s[dim - 1 - a] += 1
+        faces.append(np.full(s, 2.0))
+    faces[dim - 1][(1,) * dim] = 0.25
+    faces[dim - 2][(0,) * dim] = 9.0
+    lam = 1 + 10j
+    v = W.rhs_uniform(shape, 36)
+    r1, r2 = O.precond_apply(v.real, v.imag, 1.5, lam.real, lam.imag)
+    with csl.Plan([dev(f) for f in faces], lam) as plan:
+        assert plan.gamma == 1.5
+        out = host(plan.precondition(dev(v)))
+    assert rel(out, r1 + 1j * r2) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_rhs_is_breakdown(csl, precision, bad):
+    # a NaN or Inf placed in f on the host: the ingest's norm is not finite, so
+    # the solve ends at once with CSL_BREAKDOWN (no kernel reads past it)
+    s = W.config0()
+    f = s.f.copy()
+    f[10, 20] = complex(bad, 0.0)
+    with csl.Plan([dev(x) for x in s.faces], s.lam, precision=precision) as plan:
+        z, info = plan.solve(dev(f), tol=1e-8, maxit=100)
+        assert info.status == csl.BREAKDOWN and info.iters == 0
+        # the plan stays usable: the clean right-hand side solves as before
+        z, info = plan.solve(dev(s.f), tol=1e-8, maxit=200)
+        assert info.converged
+
+
+def test_nonfinite_coefficient_rejected(csl):
+    n = 7
+    faces = [np.array(x) for x in W.sample_faces(2, n, W.coef_c0)]
+    faces[0][2, 3] = float("nan")
+    with pytest.raises(csl.CSLError) as e:
+        csl.Plan([dev(x) for x in faces], 1 + 1j)
+    assert e.value.status == csl.INVALID_ARG
