@@ -372,13 +372,15 @@ csl_status csl_precondition_static(int dim, const int64_t n[3], double gamma, do
                                    int precision, const double* v, double* out, void* stream);
 
 /*
- * Measurement hook (not part of the method): time each kernel of one MINRES
- * iteration on the plan's stream with CUDA events, against a scratch copy of
- * the solver state so that no kernel exits early.  Each of the `reps` timed
- * groups is 4 back-to-back launches of the kernel between two events (the
- * host's submission latency is then not counted).  The vectors hold whatever
- * the last call left (run a solve first).  On return ms[i] is the mean
- * duration of one launch of kernel i and names[i] its name, for
+ * Measurement hook (not part of the method): time each kernel of the MINRES
+ * iteration with CUDA events on the plan's stream.  The iteration's kernel
+ * sequence runs `reps` (1..1000) times in a row, after one untimed
+ * iteration, with an event between consecutive kernels (the w/x update
+ * after the inverse x transform), so that each kernel is timed after its
+ * real predecessor with the caches as the iteration leaves them.  The
+ * kernels run on a scratch copy of the solver state and the vectors the last
+ * call left (run a solve first); the solver's own state is untouched.  On
+ * return ms[i] is the mean duration of kernel i and names[i] its name, for
  * i < *count (<= 8).  Synchronises the stream.
  */
 csl_status csl_time_kernels(csl_plan* plan, int reps, double ms[8], const char* names[8], int* count);

@@ -1464,26 +1464,57 @@ csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* 
   return CSL_OK;
 }
 
-// launches per timed group of csl_time_kernels
-constexpr int kTimeGroup = 4;
+// one kernel (index k of the iteration's sequence) of the MINRES iteration
+// with buffer parity par, on the plan's stream (measurement hook)
+static cudaError_t launch_iteration_kernel(csl_plan* P, int k, int par) {
+  const bool fp32 = P->precision != CSL_PREC_FP64;
+  const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
+  const int st3 = P->split_update ? STORE_Z : update_store(P);
+  if (k == 0) return fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
+  if (k == 1)
+    return fp32 ? run_row<float>(P, lanczos_load(P), STORE_T, p1_args<float>(P, par), P->stream)
+                : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
+  if (k == nkb) return fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
+  if (k == nkb - 1)
+    return fp32 ? run_row<float>(P, LOAD_T, st3, p3_args<float>(P, par), P->stream)
+                : run_row<double>(P, LOAD_T, st3, p3_args<double>(P, par), P->stream);
+  const bool mid = (P->dim == 2) || (k == 3);
+  const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
+  const int axis = (P->dim == 3 && k == 3) ? 2 : 1;
+  if (fp32) {
+    StridedArgs<float> a = strided_args<float>(P, c, axis);
+    a.st = P->st;
+    if (mid) {
+      fill_mid<float>(P, a, axis);
+      a.scalar_mode = 2;
+    }
+    return launch_strided<float>(c.N, c.wide, mid, a, c.L, P->stream);
+  }
+  StridedArgs<double> a = strided_args<double>(P, c, axis);
+  a.st = P->st;
+  if (mid) {
+    fill_mid<double>(P, a, axis);
+    a.scalar_mode = 2;
+  }
+  return launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
+}
 
 csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* names[8], int* count) {
-  if (!P || !ms || !names || !count || reps < 1) return CSL_INVALID_ARG;
+  if (!P || !ms || !names || !count || reps < 1 || reps > 1000) return CSL_INVALID_ARG;
+  // scratch solver state: a Lanczos run from the vectors the last solve left,
+  // with the stopping schedule disabled (no true-residual pass, no exit)
   DevState h;
   memset(&h, 0, sizeof(h));
   h.gam = h.gam_old = h.gam1 = 1.0;
   h.a1_old = h.a1_old2 = 1.0;
   h.c = h.c_old = 1.0;
-  h.eta = h.eta_x = h.bnorm = 1.0;
+  h.eta = h.eta_x = h.bnorm = h.r0norm = 1.0;
   h.tol = 1e-300;
   h.maxit = 1 << 30;
   h.beta = P->beta;
+  h.sqrt_pmin = h.sqrt_pmax = 1e300;
   DevState* keep = P->st;
   P->st = P->st_prof;  // all launches below read the scratch state
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t err = cudaEventCreate(&e0);
-  if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  const bool fp32 = P->precision != CSL_PREC_FP64;
   const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
   const int nk = nkb + (P->split_update ? 1 : 0);
   static const char* n2[5] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
@@ -1491,63 +1522,37 @@ csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* nam
   static const char* n3[7] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
                               "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
   static const char* p3split = "k_row<LOAD_T,STORE_Z>";
-  const int st3 = P->split_update ? STORE_Z : update_store(P);
+  // The iteration's own kernel sequence, `reps` iterations in a row on the
+  // plan's stream (the update after the inverse x transform), an event
+  // between consecutive kernels: each kernel is timed after its real
+  // predecessor, with the caches as the iteration leaves them.  One
+  // untimed iteration first.
+  std::vector<cudaEvent_t> ev((size_t)(reps + 1) * (nk + 1), nullptr);
+  cudaError_t err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
+  for (size_t i = 0; i < ev.size() && err == cudaSuccess; ++i) err = cudaEventCreate(&ev[i]);
+  for (int r = 0; r <= reps && err == cudaSuccess; ++r) {
+    cudaEvent_t* er = &ev[(size_t)r * (nk + 1)];
+    err = cudaEventRecord(er[0], P->stream);
+    for (int k = 0; k < nk && err == cudaSuccess; ++k) {
+      err = launch_iteration_kernel(P, k, r & 1);
+      if (err == cudaSuccess) err = cudaEventRecord(er[k + 1], P->stream);
+    }
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(P->stream);
   int k = 0;
   for (k = 0; k < nk && err == cudaSuccess; ++k) {
     double tot = 0.0;
-    for (int r = 0; r < reps && err == cudaSuccess; ++r) {
-      err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
-      if (err == cudaSuccess) err = cudaEventRecord(e0, P->stream);
-      if (err != cudaSuccess) break;
-      // a group of kTimeGroup back-to-back launches between the events, so
-      // that the host's submission latency is not counted in the duration
-      for (int g = 0; g < kTimeGroup && err == cudaSuccess; ++g) {
-      const int par = g & 1;
-      if (k == 0) {
-        err = fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
-      } else if (k == 1) {
-        err = fp32 ? run_row<float>(P, lanczos_load(P), STORE_T, p1_args<float>(P, par), P->stream)
-                   : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
-      } else if (k == nkb) {
-        err = fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
-      } else if (k == nkb - 1) {
-        err = fp32 ? run_row<float>(P, LOAD_T, st3, p3_args<float>(P, par), P->stream)
-                   : run_row<double>(P, LOAD_T, st3, p3_args<double>(P, par), P->stream);
-      } else {
-        const bool mid = (P->dim == 2) || (k == 3);
-        const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
-        const int axis = (P->dim == 3 && k == 3) ? 2 : 1;
-        if (fp32) {
-          StridedArgs<float> a = strided_args<float>(P, c, axis);
-          a.st = P->st;
-          if (mid) {
-            fill_mid<float>(P, a, axis);
-            a.scalar_mode = 2;
-          }
-          err = launch_strided<float>(c.N, c.wide, mid, a, c.L, P->stream);
-        } else {
-          StridedArgs<double> a = strided_args<double>(P, c, axis);
-          a.st = P->st;
-          if (mid) {
-            fill_mid<double>(P, a, axis);
-            a.scalar_mode = 2;
-          }
-          err = launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
-        }
-      }
-      }
-      if (err == cudaSuccess) err = cudaEventRecord(e1, P->stream);
-      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    for (int r = 1; r <= reps && err == cudaSuccess; ++r) {
       float t = 0.f;
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
-      tot += t / kTimeGroup;
+      err = cudaEventElapsedTime(&t, ev[(size_t)r * (nk + 1) + k], ev[(size_t)r * (nk + 1) + k + 1]);
+      tot += t;
     }
     ms[k] = tot / reps;
     names[k] = (P->split_update && k == nkb - 1) ? p3split : P->dim == 2 ? n2[k] : n3[k];
   }
   P->st = keep;
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
   *count = k;
   if (err != cudaSuccess) {
     record_error(err, "csl_time_kernels", __LINE__);

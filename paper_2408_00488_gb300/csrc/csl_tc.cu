@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* fdata = (float*)a.data;
   double g2acc = 0.0;
   int ok = 1;
+  uint32_t pending = 0;  // after a wait gave up: the parity of the commit still outstanding
 
   for (int tile = bid; tile < ntiles; tile += nblk) {
     const int o = tile / ntx;
@@ -289,8 +290,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       umma_commit(bar);
     }
     ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    if (!ok) {
+      pending = phase;
+      break;
+    }
     phase ^= 1u;
-    if (!ok) break;
     tc_fence_after();
     if (MID) {
       const bool cvalid = col0 + ec < a.ncols;
@@ -335,8 +339,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         umma_commit(bar);
       }
       ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+      if (!ok) {
+        pending = phase;
+        break;
+      }
       phase ^= 1u;
-      if (!ok) break;
       tc_fence_after();
     }
     {
@@ -360,6 +367,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     tc_fence_before();
     __syncthreads();  // operands and TMEM free for the next tile
+  }
+  if (!ok) {
+    // A wait gave up (about a second without the commit's arrival).  The
+    // MMAs of that commit may still be in flight, reading this CTA's shared
+    // memory and writing its TMEM: wait for the same commit once more,
+    // again bounded, before the TMEM is freed and the CTA exits.  No thread
+    // issues further MMAs or writes the operands after the break, so a
+    // commit that arrives within this second wait leaves nothing in flight.
+    (void)mbar_wait(bar, pending);
+    tc_fence_after();
   }
   pdl_trigger();
   tc_fence_before();
