@@ -36,6 +36,10 @@ WORKLOAD = ("config1: 2D unit square, n=1023 (M=1,046,529), 5-point FD of -div(a
             "a=exp(ln10*x*y) at face midpoints, lambda=0+100i, f~U[-1,1]^2 seed 1, tol 1e-8")
 TOL = 1e-8
 MAXIT = 2000
+HEADLINE_ARITH = ("MINRES with FP32 sine transforms and per-mode scale inside P^-1; the stencil, the Lanczos "
+                  "vectors and step and the w/x update in float-pair (double-float, about 2^-47) arithmetic; "
+                  "Lanczos/Givens scalars, reductions and the true-residual check in FP64 (a further variant of "
+                  "the FP32-preconditioner form; the form with FP64 vectors is forms.fp32_precond)")
 
 
 def read_peaks():
@@ -151,9 +155,21 @@ class ClockSampler:
 def kernel_model(name, M, d, prec, N, ff=False):
     """Algorithmic bytes and flops per launch of one kernel of a MINRES
     iteration (M grid points, d dims, line length N = n+1 of the pass axis).
+    prec: "fp64", "fp32" (FP32 transforms, float-pair vectors) or
+    "fp32_precond" (FP32 transforms, FP64 vectors and stencil).
     ff: the stencil runs in float-pair arithmetic (faces as 8-byte pairs, no
     diagonal; its FP32 instructions counted as 2 flops each, so that they
     meet the FP32 peak at the instruction issue rate)."""
+    if prec == "fp32_precond":  # the FP64 form's vector work around FP32 transforms
+        b64, f64_, f32_ = kernel_model(name, M, d, "fp64", N)
+        b32, f64t, f32t = kernel_model(name, M, d, "fp32", N)
+        if name == "k_stencil":
+            return b64 - 8 * M, f64_, 0.0  # z read as FP32
+        if name.startswith("k_row<LOAD_LANCZOS"):
+            return b64 - 8 * M, 4.0 * M, f32t - 2 * 36 * M
+        if name == "k_update":
+            return b64 - 8 * M, f64_, 0.0
+        return b32, f64t, f32t
     sT = 16 if prec == "fp64" else 8
     dst_flops = 11 + 5 * math.log2(N)  # per complex point per sine transform (pre, FFT, split, scan)
     f64 = f32 = 0.0
@@ -230,22 +246,26 @@ def roofline_table(kernels, M, d, prec, n, hbm_gbs, iters, ff=False):
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(budget_s=12.0):
-    """Time the FP64 CPU oracle on a bounded sample of the workload: k MINRES
-    iterations of the same solve; returns (seconds per iteration, k)."""
-    import numpy as np
+ORACLE_SAMPLE_ITERS = 40
+
+
+def oracle_seconds_per_iteration(k=ORACLE_SAMPLE_ITERS):
+    """One bounded sample of the FP64 CPU oracle on the workload: the first k
+    MINRES iterations of its solve (set-up included, as in a full solve);
+    returns (seconds per iteration, iterations run)."""
     import oracle
     import workloads as W
 
     s = W.config1()
     t = time.perf_counter()
-    oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=1)
-    t1 = time.perf_counter() - t
-    k = max(2, min(40, int(budget_s / max(t1, 1e-3))))
-    t = time.perf_counter()
     _, info = oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=k)
     dt = time.perf_counter() - t
     return dt / info.iters, info.iters
+
+
+def cpu_oracle_sample():
+    """The cpu_baseline leg: the same 40-iteration sample as the reference arm."""
+    return oracle_seconds_per_iteration(ORACLE_SAMPLE_ITERS)
 
 
 def run_reference(args, rank, world):
@@ -257,15 +277,12 @@ def run_reference(args, rank, world):
     import workloads as W
 
     iters_full = golden_iters("config1")
-    s = W.config1()
-    k_per_step = 3
+    k_per_step = ORACLE_SAMPLE_ITERS
     times = []
     for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        _, info = oracle.solve(s.faces, s.lam, s.f, tol=1e-300, maxit=k_per_step)
-        dt = time.perf_counter() - t
+        per, _ = oracle_seconds_per_iteration(k_per_step)
         if i >= args.warmup:
-            times.append(dt / info.iters)
+            times.append(per)
     per_iter = statistics.mean(times)
     value = 1.0 / (per_iter * iters_full) if iters_full else None
     cores = len(os.sched_getaffinity(0))
@@ -274,9 +291,11 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step = {k_per_step} MINRES iterations of the workload's solve "
-                                       f"(oracle.solve, FP64 NumPy, dense O(n^2) DST-I); solves/s = "
-                                       f"1 / (s per iteration x {iters_full} iterations of the full oracle solve)"},
+                             "sample": f"each step = the first {k_per_step} MINRES iterations of the workload's "
+                                       f"solve, set-up included (oracle.solve, FP64 NumPy, dense O(n^2) DST-I, "
+                                       f"explicit residual per iteration); solves/s = 1 / (s per iteration x "
+                                       f"{iters_full} iterations of the full oracle solve); the same sample as "
+                                       f"the cpu_baseline of the GPU arm"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -420,7 +439,7 @@ def main():
 
     forms = {}
     plans = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp32_precond", "fp64"):
         plans[prec] = csl.Plan(faces, s.lam, precision=prec, use_graph=not args.no_graph)
         z = torch.empty_like(f)
         for _ in range(args.warmup):
@@ -445,9 +464,24 @@ def main():
     clocks = sampler.stop()
     ms_mixed = max_over_ranks(ms_mixed)
     assert info_mixed.converged and info_mixed.relres <= TOL
-    forms["fp32_precond"] = {"solves_per_s": job_rate(1, world, ms_mixed), "ms_per_solve": ms_mixed,
-                             "iters": info_mixed.iters, "relres": info_mixed.relres,
-                             "launches_per_solve": info_mixed.launches}
+    forms["fp32_pairs"] = {"solves_per_s": job_rate(1, world, ms_mixed), "ms_per_solve": ms_mixed,
+                           "iters": info_mixed.iters, "oracle_iters": golden_iters("config1"),
+                           "relres": info_mixed.relres, "launches_per_solve": info_mixed.launches,
+                           "arithmetic": HEADLINE_ARITH}
+
+    # ---- FP32 only inside P^-1, every vector and the stencil in FP64 --------
+    barrier()
+    ms_sp, info_sp = timed(lambda: plans["fp32_precond"].solve(f, tol=TOL, maxit=MAXIT, out=z)[1], args.steps,
+                           "timed_fp32_precond")
+    barrier()
+    ms_sp = max_over_ranks(ms_sp)
+    assert info_sp.converged and info_sp.relres <= TOL
+    forms["fp32_precond"] = {"solves_per_s": job_rate(1, world, ms_sp), "ms_per_solve": ms_sp,
+                             "iters": info_sp.iters, "oracle_iters": golden_iters("config1"),
+                             "relres": info_sp.relres, "launches_per_solve": info_sp.launches,
+                             "arithmetic": "FP32 sine transforms and per-mode scale inside P^-1; stencil, "
+                                           "Lanczos vectors and step, w/x update, Givens, reductions and "
+                                           "residual check in FP64"}
 
     # ---- plain FP64 form ---------------------------------------------------
     barrier()
@@ -456,7 +490,8 @@ def main():
     ms_64 = max_over_ranks(ms_64)
     assert info_64.converged and info_64.relres <= TOL
     forms["fp64"] = {"solves_per_s": job_rate(1, world, ms_64), "ms_per_solve": ms_64, "iters": info_64.iters,
-                     "relres": info_64.relres, "launches_per_solve": info_64.launches}
+                     "oracle_iters": golden_iters("config1"), "relres": info_64.relres,
+                     "launches_per_solve": info_64.launches, "arithmetic": "FP64 throughout (the paper's)"}
 
     # ---- end to end through the C ABI with host buffers (pinned) -------------
     fh = torch.from_numpy(np.ascontiguousarray(s.f)).pin_memory()
@@ -471,13 +506,13 @@ def main():
 
     # ---- per-kernel durations (CUDA events on the launching stream) --------
     kern = {}
-    for prec, key in (("fp32", "fp32_precond"), ("fp64", "fp64")):
+    for prec, key in (("fp32", "fp32_pairs"), ("fp32_precond", "fp32_precond"), ("fp64", "fp64")):
         p = plans[prec]
         p.solve(f, tol=TOL, maxit=MAXIT, out=z)  # real data in the vectors
         kt = p.time_kernels(args.kernel_reps)
         kern[key] = roofline_table(kt, M, d, prec, n, hbm_gbs, forms[key]["iters"],
                                    ff="stencil[float-pair" in p.config)
-    head = kern["fp32_precond"]
+    head = kern["fp32_pairs"]
     dom = max(head, key=lambda r: r["ms"])
     roofline = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"],
                 "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
@@ -629,8 +664,10 @@ def main():
         line = {
             "metric": METRIC, "value": job_rate(1, world, ms_mixed), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (float-pair vectors; f64 scalars and residual check; f32 inside P^-1)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "FP32-preconditioner MINRES (FP64 stencil/Lanczos/Givens)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inside P^-1; f32x2 float-pair vectors and stencil; f64 scalars and residual check",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": HEADLINE_ARITH,
                        "l2": "flushed (256 MiB write) before every step", "parallelism": "replicas" if world > 1
                        else "single GPU"},
             "forms": forms,
@@ -640,7 +677,8 @@ def main():
             "config2_forms": cfg2,
             "paradiag": pdline,
             "paper_tables": tables,
-            "plan_config": {k: plans[p].config for k, p in (("fp32_precond", "fp32"), ("fp64", "fp64"))},
+            "plan_config": {k: plans[p].config for k, p in (("fp32_pairs", "fp32"), ("fp32_precond", "fp32_precond"),
+                                                             ("fp64", "fp64"))},
             "kernels": kern,
             "cpu_baseline": cpu,
             "e2e": {"value": job_rate(1, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": bytes_io,

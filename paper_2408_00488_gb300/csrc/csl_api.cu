@@ -579,12 +579,101 @@ cudaError_t launch_precondition_T(csl_plan* P, const double2* v, double2* out, c
   return e;
 }
 
+// one kernel (index k of the iteration's sequence) of the MINRES iteration
+// with buffer parity par, on the plan's stream (measurement and tuning);
+// mid_mode: the MID pass's scalar tail (2: Givens step, 0: none)
+cudaError_t launch_iteration_kernel(csl_plan* P, int k, int par, int mid_mode) {
+  const bool fp32 = P->precision != CSL_PREC_FP64;
+  const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
+  const int st3 = P->split_update ? STORE_Z : update_store(P);
+  if (k == 0) return fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
+  if (k == 1)
+    return fp32 ? run_row<float>(P, lanczos_load(P), STORE_T, p1_args<float>(P, par), P->stream)
+                : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
+  if (k == nkb) return fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
+  if (k == nkb - 1)
+    return fp32 ? run_row<float>(P, LOAD_T, st3, p3_args<float>(P, par), P->stream)
+                : run_row<double>(P, LOAD_T, st3, p3_args<double>(P, par), P->stream);
+  const bool mid = (P->dim == 2) || (k == 3);
+  const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
+  const int axis = (P->dim == 3 && k == 3) ? 2 : 1;
+  if (fp32) {
+    StridedArgs<float> a = strided_args<float>(P, c, axis);
+    a.st = P->st;
+    if (mid) {
+      fill_mid<float>(P, a, axis);
+      a.scalar_mode = mid_mode;
+    }
+    return launch_strided<float>(c.N, c.wide, mid, a, c.L, P->stream);
+  }
+  StridedArgs<double> a = strided_args<double>(P, c, axis);
+  a.st = P->st;
+  if (mid) {
+    fill_mid<double>(P, a, axis);
+    a.scalar_mode = mid_mode;
+  }
+  return launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
+}
+
+
+// Number of kernels of one iteration in csl_time_kernels' order: stencil,
+// P1, [3D: y fwd,] MID, [3D: y inv,] P3, and the update when it is its own kernel
+int iteration_kernels(const csl_plan* P) { return (P->dim == 2 ? 4 : 6) + (P->split_update ? 1 : 0); }
+
+// The iteration's kernel sequence, `reps` iterations in a row on the plan's
+// stream after one untimed iteration, an event between consecutive kernels
+// (the update after the inverse x transform); ms[k] = mean duration of
+// kernel k.  The caller points P->st at a scratch state.  ev: at least
+// (reps + 1) * (iteration_kernels(P) + 1) created events.
+cudaError_t time_sequence(csl_plan* P, int reps, int mid_mode, cudaEvent_t* ev, double* ms) {
+  const int nk = iteration_kernels(P);
+  cudaError_t err = cudaSuccess;
+  for (int r = 0; r <= reps && err == cudaSuccess; ++r) {
+    cudaEvent_t* er = ev + (size_t)r * (nk + 1);
+    err = cudaEventRecord(er[0], P->stream);
+    for (int k = 0; k < nk && err == cudaSuccess; ++k) {
+      err = launch_iteration_kernel(P, k, r & 1, mid_mode);
+      if (err == cudaSuccess) err = cudaEventRecord(er[k + 1], P->stream);
+    }
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(P->stream);
+  for (int k = 0; k < nk && err == cudaSuccess; ++k) {
+    double tot = 0.0;
+    for (int r = 1; r <= reps && err == cudaSuccess; ++r) {
+      float t = 0.f;
+      err = cudaEventElapsedTime(&t, ev[(size_t)r * (nk + 1) + k], ev[(size_t)r * (nk + 1) + k + 1]);
+      tot += t;
+    }
+    ms[k] = tot / reps;
+  }
+  return err;
+}
+
+// scratch solver state for timing: a Lanczos run with the stopping schedule
+// disabled (no true-residual pass, no exit)
+DevState scratch_state(const csl_plan* P) {
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.gam = h.gam_old = h.gam1 = 1.0;
+  h.a1_old = h.a1_old2 = 1.0;
+  h.c = h.c_old = 1.0;
+  h.eta = h.eta_x = h.bnorm = h.r0norm = 1.0;
+  h.tol = 1e-300;
+  h.maxit = 1 << 30;
+  h.beta = P->beta;
+  h.sqrt_pmin = h.sqrt_pmax = 1e300;
+  return h;
+}
+
 // ---- autotuner ---------------------------------------------------------------
-// Each sine-transform pass is timed (CUDA events on the plan's stream, the
-// plan's own buffers, a scratch solver state; the fastest of 5 launches) for
-// every CTA size and, for N = 512 and 1024, every transform variant; the
-// fastest candidate is kept.  Results are
-// cached per (precision, pass, geometry) for the life of the process.
+// Each sine-transform pass tries every CTA size and, for N = 512 and 1024,
+// every transform variant.  A candidate is timed inside the iteration's own
+// kernel sequence (time_sequence: three iterations after a warm-up, on
+// zeroed vectors and a scratch state, the MID pass without its scalar tail),
+// so that its cost includes the caches and the predecessor it really has;
+// the candidate with the smallest summed duration of the pass's kernels is
+// kept.  Results are cached per (precision, pass, geometry) for the life of
+// the process, and can be saved to and loaded from a file.
 struct TuneKey {
   int prec, kind, N, ncols, nouter;
   bool operator<(const TuneKey& o) const {
@@ -597,31 +686,6 @@ struct TuneKey {
 };
 std::map<TuneKey, PassCfg> g_tune_cache;
 std::mutex g_tune_mu;
-
-// launch the pass `kind` once with configuration c: 0 = row pass (P1 + P3 of
-// an iteration), 1 = strided plain, 2 = strided mid
-template <typename T>
-cudaError_t tune_launch(csl_plan* P, int kind, const PassCfg& c, int axis) {
-  if (kind == 0) {
-    const PassCfg keep = P->row;
-    P->row = c;
-    cudaError_t e = run_row<T>(P, lanczos_load(P), STORE_T, p1_args<T>(P, 0), P->stream);
-    // P3 as the solve runs it (the update on its own branch, or fused)
-    if (e == cudaSuccess)
-      e = run_row<T>(P, LOAD_T, P->split_update ? STORE_Z : update_store(P), p3_args<T>(P, 0), P->stream);
-    P->row = keep;
-    return e;
-  }
-  StridedArgs<T> a = strided_args<T>(P, c, axis);
-  a.st = P->st;
-  if (kind == 2) {
-    fill_mid<T>(P, a, axis);
-    // no Givens tail while tuning: on the zero tuning data it would end the
-    // scratch solve, and the next launch of a timed group would return at once
-    a.scalar_mode = 0;
-  }
-  return launch_strided<T>(c.N, c.wide, kind == 2, a, c.L, P->stream);
-}
 
 // One candidate shape of a pass: transform variant w with `lines` lines per
 // CTA; false when the shape is not allowed (CTA size, shared memory, tile
@@ -650,9 +714,26 @@ bool make_candidate(const PassCfg& c, int kind, int w, int lines, PassCfg& cand)
   return true;
 }
 
+// the kernels of the sequence that a pass's shape governs (kind 0: the row
+// passes P1 and P3; kind 1: the 3D y passes; kind 2: the MID pass)
+int pass_kernels(const csl_plan* P, int kind, int idx[2]) {
+  const int nkb = P->dim == 2 ? 4 : 6;
+  if (kind == 0) {
+    idx[0] = 1;
+    idx[1] = nkb - 1;
+    return 2;
+  }
+  if (kind == 1) {
+    idx[0] = 2;
+    idx[1] = 4;
+    return 2;
+  }
+  idx[0] = P->dim == 2 ? 2 : 3;
+  return 1;
+}
+
 template <typename T>
-cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e0, cudaEvent_t e1,
-                      const DevState& hst) {
+cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, cudaEvent_t* ev, const DevState& hst) {
   if (c.L.tc || c.wide >= 3) return cudaSuccess;  // the tensor-core and long-line variants have one shape
   const TuneKey key = {(int)sizeof(T), kind, c.N, c.ncols, c.nouter};
   {
@@ -662,41 +743,39 @@ cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e
       PassCfg hit;
       // a cached shape is rebuilt from (variant, lines) for this plan's pass
       if (make_candidate<T>(c, kind, it->second.wide, it->second.lines, hit)) {
-        hit.L.pdl = c.L.pdl;
         c = hit;
         return cudaSuccess;
       }
     }
   }
+  int idx[2];
+  const int nidx = pass_kernels(P, kind, idx);
+  const PassCfg keep = c;
   PassCfg best = c;
-  float best_ms = 1e30f;
-  for (int w = 0; w < pass_num_variants(c.N); ++w) {
-    for (int lines = 1; lines <= 256; lines <<= 1) {
+  double best_ms = 1e30;
+  double ms[8];
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < pass_num_variants(keep.N) && e == cudaSuccess; ++w) {
+    for (int lines = 1; lines <= 256 && e == cudaSuccess; lines <<= 1) {
       PassCfg cand;
-      if (!make_candidate<T>(c, kind, w, lines, cand)) continue;
-      // the fastest of 5 timed groups (after one warm-up) of 3 back-to-back
-      // launches: the host's submission hides behind the GPU's execution, and
-      // a group delayed by something else on the GPU is discarded
-      float tot = 1e30f;
-      cudaError_t e = cudaSuccess;
-      for (int r = 0; r < 6 && e == cudaSuccess; ++r) {
+      if (!make_candidate<T>(keep, kind, w, lines, cand)) continue;
+      c = cand;  // c is the plan's own pass configuration
+      double t = 1e30;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the faster of two measurements
         e = cudaMemcpyAsync(P->st, &hst, sizeof(hst), cudaMemcpyHostToDevice, P->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = tune_launch<T>(P, kind, cand, axis);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-        if (r > 0 && t < tot) tot = t;
+        if (e == cudaSuccess) e = time_sequence(P, 3, 0, ev, ms);
+        double sum = 0.0;
+        for (int i = 0; i < nidx; ++i) sum += ms[idx[i]];
+        if (e == cudaSuccess && sum < t) t = sum;
       }
-      if (e != cudaSuccess) return e;
-      if (tot < best_ms) {
-        best_ms = tot;
+      if (e == cudaSuccess && t < best_ms) {
+        best_ms = t;
         best = cand;
       }
     }
   }
   c = best;
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best;
   return cudaSuccess;
@@ -704,37 +783,30 @@ cudaError_t tune_pass(csl_plan* P, PassCfg& c, int kind, int axis, cudaEvent_t e
 
 template <typename T>
 cudaError_t autotune(csl_plan* P) {
-  DevState h;
-  memset(&h, 0, sizeof(h));
-  h.gam = h.gam_old = h.gam1 = 1.0;
-  h.a1_old = h.a1_old2 = 1.0;
-  h.c = h.c_old = 1.0;
-  h.eta = h.eta_x = h.bnorm = 1.0;
-  h.tol = 1e-300;
-  h.maxit = 1 << 30;
-  h.beta = P->beta;
+  const DevState h = scratch_state(P);
   DevState* keep = P->st;
   P->st = P->st_prof;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  // the vectors are uninitialised here: give the row pass finite inputs
+  std::vector<cudaEvent_t> ev((size_t)4 * (iteration_kernels(P) + 1), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  // the vectors are uninitialised here: zero them (finite inputs for every pass)
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(P->v[i], 0, sizeof(double2) * P->M, P->stream);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(P->w[i], 0, sizeof(double2) * P->M, P->stream);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaMemsetAsync(P->z[i], 0, sizeof(typename C2<T>::t) * P->M, P->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->x, 0, sizeof(double2) * P->M, P->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->b, 0, sizeof(double2) * P->M, P->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->T, 0, sizeof(typename C2<T>::t) * P->M, P->stream);
-  if (e == cudaSuccess) e = tune_pass<T>(P, P->row, 0, 0, e0, e1, h);
+  if (e == cudaSuccess) e = tune_pass<T>(P, P->row, 0, ev.data(), h);
   if (P->dim == 2) {
-    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 2, 1, e0, e1, h);
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 2, ev.data(), h);
   } else {
-    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 1, 1, e0, e1, h);
-    if (e == cudaSuccess) e = tune_pass<T>(P, P->sz, 2, 2, e0, e1, h);
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sy, 1, ev.data(), h);
+    if (e == cudaSuccess) e = tune_pass<T>(P, P->sz, 2, ev.data(), h);
   }
   P->st = keep;
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
   return e;
 }
 
@@ -1464,101 +1536,41 @@ csl_status csl_coef_grad(csl_plan* P, const double* z, const double* y, double* 
   return CSL_OK;
 }
 
-// one kernel (index k of the iteration's sequence) of the MINRES iteration
-// with buffer parity par, on the plan's stream (measurement hook)
-static cudaError_t launch_iteration_kernel(csl_plan* P, int k, int par) {
-  const bool fp32 = P->precision != CSL_PREC_FP64;
-  const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
-  const int st3 = P->split_update ? STORE_Z : update_store(P);
-  if (k == 0) return fp32 ? launch_stencil<float>(P, par, P->stream, false) : launch_stencil<double>(P, par, P->stream, false);
-  if (k == 1)
-    return fp32 ? run_row<float>(P, lanczos_load(P), STORE_T, p1_args<float>(P, par), P->stream)
-                : run_row<double>(P, LOAD_LANCZOS, STORE_T, p1_args<double>(P, par), P->stream);
-  if (k == nkb) return fp32 ? launch_update<float>(P, par, P->stream) : launch_update<double>(P, par, P->stream);
-  if (k == nkb - 1)
-    return fp32 ? run_row<float>(P, LOAD_T, st3, p3_args<float>(P, par), P->stream)
-                : run_row<double>(P, LOAD_T, st3, p3_args<double>(P, par), P->stream);
-  const bool mid = (P->dim == 2) || (k == 3);
-  const PassCfg& c = (P->dim == 3 && k == 3) ? P->sz : P->sy;
-  const int axis = (P->dim == 3 && k == 3) ? 2 : 1;
-  if (fp32) {
-    StridedArgs<float> a = strided_args<float>(P, c, axis);
-    a.st = P->st;
-    if (mid) {
-      fill_mid<float>(P, a, axis);
-      a.scalar_mode = 2;
-    }
-    return launch_strided<float>(c.N, c.wide, mid, a, c.L, P->stream);
-  }
-  StridedArgs<double> a = strided_args<double>(P, c, axis);
-  a.st = P->st;
-  if (mid) {
-    fill_mid<double>(P, a, axis);
-    a.scalar_mode = 2;
-  }
-  return launch_strided<double>(c.N, c.wide, mid, a, c.L, P->stream);
-}
-
 csl_status csl_time_kernels(csl_plan* P, int reps, double ms[8], const char* names[8], int* count) {
   if (!P || !ms || !names || !count || reps < 1 || reps > 1000) return CSL_INVALID_ARG;
-  // scratch solver state: a Lanczos run from the vectors the last solve left,
-  // with the stopping schedule disabled (no true-residual pass, no exit)
-  DevState h;
-  memset(&h, 0, sizeof(h));
-  h.gam = h.gam_old = h.gam1 = 1.0;
-  h.a1_old = h.a1_old2 = 1.0;
-  h.c = h.c_old = 1.0;
-  h.eta = h.eta_x = h.bnorm = h.r0norm = 1.0;
-  h.tol = 1e-300;
-  h.maxit = 1 << 30;
-  h.beta = P->beta;
-  h.sqrt_pmin = h.sqrt_pmax = 1e300;
+  *count = 0;
+  const DevState h = scratch_state(P);
   DevState* keep = P->st;
   P->st = P->st_prof;  // all launches below read the scratch state
   const int nkb = P->dim == 2 ? 4 : 6;  // kernels of the main chain
-  const int nk = nkb + (P->split_update ? 1 : 0);
+  const int nk = iteration_kernels(P);
   static const char* n2[5] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<mid>",
                               "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
   static const char* n3[7] = {"k_stencil", "k_row<LOAD_LANCZOS,STORE_T>", "k_strided<y>", "k_strided<mid>",
                               "k_strided<y>(inverse)", "k_row<LOAD_T,STORE_Z_UPDATE>", "k_update"};
   static const char* p3split = "k_row<LOAD_T,STORE_Z>";
-  // The iteration's own kernel sequence, `reps` iterations in a row on the
-  // plan's stream (the update after the inverse x transform), an event
-  // between consecutive kernels: each kernel is timed after its real
-  // predecessor, with the caches as the iteration leaves them.  One
-  // untimed iteration first.
   std::vector<cudaEvent_t> ev((size_t)(reps + 1) * (nk + 1), nullptr);
   cudaError_t err = cudaMemcpyAsync(P->st_prof, &h, sizeof(h), cudaMemcpyHostToDevice, P->stream);
   for (size_t i = 0; i < ev.size() && err == cudaSuccess; ++i) err = cudaEventCreate(&ev[i]);
-  for (int r = 0; r <= reps && err == cudaSuccess; ++r) {
-    cudaEvent_t* er = &ev[(size_t)r * (nk + 1)];
-    err = cudaEventRecord(er[0], P->stream);
-    for (int k = 0; k < nk && err == cudaSuccess; ++k) {
-      err = launch_iteration_kernel(P, k, r & 1);
-      if (err == cudaSuccess) err = cudaEventRecord(er[k + 1], P->stream);
-    }
-  }
+  if (err == cudaSuccess) err = time_sequence(P, reps, 2, ev.data(), ms);
+  // the scratch run must not have ended (a breakdown would let kernels exit at entry)
+  DevState after;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&after, P->st_prof, sizeof(after), cudaMemcpyDeviceToHost, P->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(P->stream);
-  int k = 0;
-  for (k = 0; k < nk && err == cudaSuccess; ++k) {
-    double tot = 0.0;
-    for (int r = 1; r <= reps && err == cudaSuccess; ++r) {
-      float t = 0.f;
-      err = cudaEventElapsedTime(&t, ev[(size_t)r * (nk + 1) + k], ev[(size_t)r * (nk + 1) + k + 1]);
-      tot += t;
-    }
-    ms[k] = tot / reps;
-    names[k] = (P->split_update && k == nkb - 1) ? p3split : P->dim == 2 ? n2[k] : n3[k];
-  }
   P->st = keep;
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
-  *count = k;
   if (err != cudaSuccess) {
     record_error(err, "csl_time_kernels", __LINE__);
     (void)cudaGetLastError();
     return CSL_CUDA_ERROR;
   }
+  if (after.done) {
+    csl_internal_set_error("csl_time_kernels: the scratch iteration ended early; the timings are not valid");
+    return CSL_BREAKDOWN;
+  }
+  for (int k = 0; k < nk; ++k) names[k] = (P->split_update && k == nkb - 1) ? p3split : P->dim == 2 ? n2[k] : n3[k];
+  *count = nk;
   return CSL_OK;
 }
 

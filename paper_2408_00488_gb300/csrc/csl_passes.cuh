@@ -165,9 +165,25 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     const int row = row0 + myl;
     const bool valid = row < a.nrows;
     const long base = (long)row * n;
+    if constexpr (LOAD == LOAD_T) {
+      // global -> shared copies (cp.async): every element of the lane in
+      // flight at once, no registers held; rows past the end are zero-filled
+#pragma unroll
+      for (int k = 0; k < NL; ++k) {
+        const int j = t + TPL * k;
+        if (j < n) {
+          if constexpr (sizeof(T) == 4)
+            cp_async8(&line[D::in_pos(j + 1)], valid ? (const void*)(a.tin + base + j) : (const void*)a.tin, valid);
+          else
+            cp_async16(&line[D::in_pos(j + 1)], valid ? (const void*)(a.tin + base + j) : (const void*)a.tin, valid);
+        }
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
     // global loads in batches of UB elements per lane, all issued before use
 #pragma unroll
-    for (int i0 = 0; i0 < NL; i0 += UB) {
+    for (int i0 = 0; i0 < (LOAD == LOAD_T ? 0 : NL); i0 += UB) {
       if constexpr (LOAD == LOAD_LANCZOS && pairs) {
         // pair-vector forms: u' and v_j are float pairs (re.hi, re.lo, im.hi, im.lo);
         // v_{j+1} = u' - (delta/gamma) v_j in pair arithmetic, stored
@@ -378,24 +394,24 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     const int Ch = min(C, a.ncols - col0);
     const long base = (long)o * a.outer_stride + col0;
     __syncthreads();  // tables loaded / previous tile stored
-    // blockDim = C * TPL, so NL rounds per thread cover the C x n tile; loads
-    // are batched UB at a time so that they are all in flight together
+    // blockDim = C * TPL, so NL rounds per thread cover the C x n tile; the
+    // elements are copied global -> shared with cp.async, all in flight at
+    // once (columns past the grid's edge are zero-filled)
 #pragma unroll
-    for (int q0 = 0; q0 < NL; q0 += UB) {
-      c_t v[UB];
-#pragma unroll
-      for (int k = 0; k < UB; ++k) {
-        const int e = threadIdx.x + blockDim.x * (q0 + k);
-        const int c = e & (C - 1), j = e >> logC;
-        v[k] = (c < Ch && j < n) ? a.data[base + (long)j * a.line_stride + c] : mkc<T>((T)0, (T)0);
-      }
-#pragma unroll
-      for (int k = 0; k < UB; ++k) {
-        const int e = threadIdx.x + blockDim.x * (q0 + k);
-        const int c = e & (C - 1), j = e >> logC;
-        if (j < n) lines[(size_t)c * LS + D::in_pos(j + 1)] = v[k];
+    for (int k = 0; k < NL; ++k) {
+      const int e = threadIdx.x + blockDim.x * k;
+      const int c = e & (C - 1), j = e >> logC;
+      if (j < n) {
+        const bool ok = c < Ch;
+        const c_t* src = ok ? a.data + base + (long)j * a.line_stride + c : a.data;
+        if constexpr (sizeof(T) == 4)
+          cp_async8(&lines[(size_t)c * LS + D::in_pos(j + 1)], src, ok);
+        else
+          cp_async16(&lines[(size_t)c * LS + D::in_pos(j + 1)], src, ok);
       }
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     D::template run<false>(line, t, s_tw, s_hs, s_tp, s_scr);
     if (MID) {

@@ -25,6 +25,17 @@ def test_bytes_per_point(prec, sT):
     assert per["k_update"] == sT + 80
 
 
+def test_fp32_precond_form_bytes_and_fp64_work():
+    # FP32 transforms (8-byte T, z), FP64 vectors: the stencil reads an FP32 z
+    # and FP64 faces/diagonal; the Lanczos step and the update are FP64
+    per = {nm: bench.kernel_model(nm, M, 2, "fp32_precond", 1024) for nm in NAMES_2D}
+    assert per["k_stencil"][0] / M == 8 + 16 + 16 + 8 + 16 and per["k_stencil"][1] > 0
+    assert per["k_row<LOAD_LANCZOS,STORE_T>"][0] / M == 16 + 16 + 16 + 8
+    assert per["k_row<LOAD_LANCZOS,STORE_T>"][1] / M == 4
+    assert per["k_update"][0] / M == 8 + 80 and per["k_update"][1] > 0
+    assert per["k_strided<mid>"][0] / M == 16 and per["k_strided<mid>"][1] == 0
+
+
 def test_fp32_forms_have_no_fp64_vector_work():
     for nm in NAMES_2D:
         _, f64, _ = bench.kernel_model(nm, M, 2, "fp32", 1024, ff=True)
