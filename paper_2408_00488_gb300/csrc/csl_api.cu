@@ -655,7 +655,7 @@ DevState scratch_state(const csl_plan* P) {
   DevState h;
   memset(&h, 0, sizeof(h));
   h.gam = h.gam_old = h.gam1 = 1.0;
-  h.a1_old = h.a1_old2 = 1.0;
+  h.a1inv_old = h.a1inv_old2 = 1.0;
   h.c = h.c_old = 1.0;
   h.eta = h.eta_x = h.bnorm = h.r0norm = 1.0;
   h.tol = 1e-300;

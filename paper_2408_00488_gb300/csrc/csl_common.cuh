@@ -86,8 +86,9 @@ struct DevState {
   double c, c_old, s, s_old, eta;
   // coefficients of the update w_{j+1} = w_a z_j + w_b w_{j-1} + w_c w_j, x += x_coef w_{j+1};
   // the w vectors are kept scaled by the a1 of the step that made them
-  // (w_a = 1), a1_old / a1_old2 being those of the last two steps
-  double w_a, w_b, w_c, x_coef, a1_old, a1_old2;
+  // (w_a = 1); a1inv_old / a1inv_old2 are the reciprocals of the a1 of the
+  // last two steps
+  double w_a, w_b, w_c, x_coef, a1inv_old, a1inv_old2;
   double bnorm, tol;
   double rho;     // calibrated ratio ||b - A x||_2 / |eta| (residual 2-norm per P^{-1}-norm)
   double relres;  // last explicitly evaluated true relative residual
@@ -97,10 +98,25 @@ struct DevState {
   double r0norm;  // ||b - A x_0||_2 of the start vector (= bnorm for x_0 = 0)
   double* hist;   // optional: |eta_j| / gamma_1 of every iteration j (hist_cap entries), or null
   int hist_cap;
+  int entries;    // Givens steps started (MID passes): a loop bound that needs no reduction
   int iter;       // completed iterations = index of the current iterate x
   int maxit, done, status, check, lucky, checks, calibrated, loops;
   unsigned int tickets[4];
 };
+
+static_assert(sizeof(DevState) % 4 == 0, "DevState is copied as 32-bit words");
+
+// Copy of the solver state into shared memory, taken when a kernel starts
+// (after its predecessor completed), so that the scalar step at its end does
+// not wait on a global round trip.  Only that step changes the scalars while
+// the kernel runs; the reduction tickets do change (other CTAs may have
+// arrived before this one started), so a scalar step writes back the fields
+// it sets, never the whole copy.  Block-wide; a barrier must separate it from
+// the reads.
+__device__ __forceinline__ void state_prefetch(DevState* dst, const DevState* st) {
+  constexpr int W = (int)(sizeof(DevState) / 4);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) ((unsigned*)dst)[i] = ((const unsigned*)st)[i];
+}
 
 enum { TICKET_STENCIL = 0, TICKET_MID = 1, TICKET_INGEST = 2, TICKET_AUX = 3 };  // TICKET_AUX: warm start
 

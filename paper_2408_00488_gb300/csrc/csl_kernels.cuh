@@ -428,11 +428,24 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
   const StencilArgs a = batch ? batch[sys] : a0;
   DevState* st = a.st;
   pdl_wait();
-  if (st->done) {
-    // keep the device-side loop closed whatever set `done` (Givens breakdown, cap, ...)
-    if (a.use_cond && bid == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+  // `entries` counts the Givens steps (the MID pass of each iteration adds
+  // one; nothing changes it while this kernel runs, so every CTA reads the
+  // same value): a bound on the device-side loop that does not rely on the
+  // scalar step at the end of this pass
+  const bool over = st->entries > st->maxit + 8;
+  if (st->done || over) {
+    if (bid == 0 && threadIdx.x == 0) {
+      if (!st->done) {
+        st->status = ST_NOT_CONVERGED;
+        st->done = 1;
+      }
+      // keep the device-side loop closed whatever set `done`
+      if (a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+    }
     return;
   }
+  __shared__ DevState s_pre;  // for the scalar step at the end
+  state_prefetch(&s_pre, st);
   // z_j arrives normalised (z_j / gamma_j), so A z_j needs no scaling
   const double gam = st->gam, gam_old = st->gam_old, beta = st->beta;
   const double lanc = gam / gam_old;
@@ -652,32 +665,46 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(St
   double tot[2];
   if (!grid_sum_last_block<2>(acc, a.partials, &st->tickets[TICKET_STENCIL], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
-  // scalar step after the stencil: delta_j and the stopping test for x_{iter}
-  st->delta = tot[0];
+  // scalar step after the stencil: delta_j and the stopping test for x_{iter}.
+  // It runs on a register copy of the state, loaded once and stored once: a
+  // read-modify-write chain through global memory would cost an L2 round
+  // trip per dependent access on this single thread.
+  DevState q = s_pre;
+  q.delta = tot[0];
   if (check) {
     const double rnorm = sqrt(tot[1]);
-    const double rel = rnorm / st->bnorm;
-    st->relres = rel;
-    st->checks += 1;
-    st->check = 0;
-    if (rel <= st->tol) {
-      st->done = 1;
-      st->status = ST_OK;
-    } else if (st->lucky || st->iter >= st->maxit || !(rel == rel)) {
-      st->done = 1;
-      st->status = (rel == rel) ? ST_NOT_CONVERGED : ST_BREAKDOWN;
-    } else if (st->eta_x > 0.0) {
-      st->rho = rnorm / st->eta_x;  // calibrate the 2-norm / P^{-1}-norm ratio
-      st->calibrated = 1;
+    const double rel = rnorm / q.bnorm;
+    q.relres = rel;
+    q.checks += 1;
+    q.check = 0;
+    if (rel <= q.tol) {
+      q.done = 1;
+      q.status = ST_OK;
+    } else if (q.lucky || q.iter >= q.maxit || !(rel == rel)) {
+      q.done = 1;
+      q.status = (rel == rel) ? ST_NOT_CONVERGED : ST_BREAKDOWN;
+    } else if (q.eta_x > 0.0) {
+      q.rho = rnorm / q.eta_x;  // calibrate the 2-norm / P^{-1}-norm ratio
+      q.calibrated = 1;
     }
   }
-  if (!st->done && !(st->delta == st->delta)) {
-    st->done = 1;
-    st->status = ST_BREAKDOWN;
+  if (!q.done && !(q.delta == q.delta)) {
+    q.done = 1;
+    q.status = ST_BREAKDOWN;
   }
-  st->loops += 1;
-  if (st->iter > st->maxit + 1 || st->loops > st->maxit + 4) st->done = 1;  // hard caps (integers only)
-  if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
+  q.loops += 1;
+  if (q.iter > q.maxit + 1 || q.loops > q.maxit + 4) q.done = 1;  // hard caps (integers only)
+  // the fields this step sets (the copy's tickets and entry count may be stale)
+  st->delta = q.delta;
+  st->relres = q.relres;
+  st->checks = q.checks;
+  st->check = q.check;
+  st->rho = q.rho;
+  st->calibrated = q.calibrated;
+  st->loops = q.loops;
+  st->status = q.status;
+  st->done = q.done;
+  if (a.use_cond) cudaGraphSetConditional(a.cond, q.done ? 0u : 1u);
 }
 
 // (K + lambda I) z in complex form for csl_apply.  With x = (Re z, Im z),
@@ -703,35 +730,69 @@ __global__ void __launch_bounds__(256) k_apply(Grid g, const double2* z, double2
 // of w and x, and decide whether the next stencil pass evaluates the true
 // residual.
 // ---------------------------------------------------------------------------
+// The fields the Givens step (or the start of MINRES) sets, from the register
+// copy q to the state in memory.
+__device__ __forceinline__ void store_scalar_fields(DevState* st, const DevState& q) {
+  st->w_a = q.w_a;
+  st->w_b = q.w_b;
+  st->w_c = q.w_c;
+  st->x_coef = q.x_coef;
+  st->a1inv_old = q.a1inv_old;
+  st->a1inv_old2 = q.a1inv_old2;
+  st->eta = q.eta;
+  st->eta_x = q.eta_x;
+  st->c_old = q.c_old;
+  st->c = q.c;
+  st->s_old = q.s_old;
+  st->s = q.s;
+  st->gam_old = q.gam_old;
+  st->gam = q.gam;
+  st->gam1 = q.gam1;
+  st->rho = q.rho;
+  st->iter = q.iter;
+  st->check = q.check;
+  st->lucky = q.lucky;
+  st->status = q.status;
+  st->done = q.done;
+}
+
+// st: the caller's register copy of the solver state (see mid_scalar_tail).
+// It runs on one thread, where FP64 is latency-bound on GB300 (a dependent
+// FMA about 67 cycles, a division about 440, a square root about 700), so
+// the chain is kept short: a1 = sqrt(a0^2 + g2) does not wait for gn =
+// sqrt(g2), one reciprocal 1/a1 serves cn, sn and the x coefficient, and the
+// reciprocals of the last two a1 are kept in the state for the w coefficients.
 __device__ inline void givens_step(DevState* st, double g2) {
   if (!(g2 >= 0.0) || !(g2 < 1e300)) {
     st->done = 1;
     st->status = ST_BREAKDOWN;
     return;
   }
-  const double gn = sqrt(g2);
   const double gam = st->gam, delta = st->delta;
   const double c = st->c, c_old = st->c_old, s = st->s, s_old = st->s_old;
   const double a0 = c * delta - c_old * s * gam;
-  const double a1 = sqrt(a0 * a0 + gn * gn);
+  const double gn = sqrt(g2);
+  const double a1 = sqrt(fma(a0, a0, g2));
   const double a2 = s * delta + c_old * c * gam;
   const double a3 = s_old * gam;
+  // w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j) / a1 with z_j stored normalised
+  // (z_j / gamma_j); the buffers hold w_k scaled by the a1 that made it, so
+  // that the update needs no product with z: a1 w_{j+1} = z_j - (a3/a1'') (a1'' w_{j-1})
+  // - (a2/a1') (a1' w_j), and x += (c_{j+1} eta / a1) (a1 w_{j+1})
+  const double wb = -a3 * st->a1inv_old2, wc = -a2 * st->a1inv_old;
   if (!(a1 > 0.0) || !(a1 < 1e300)) {
     st->done = 1;
     st->status = ST_BREAKDOWN;
     return;
   }
-  const double cn = a0 / a1, sn = gn / a1;
-  // w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j) / a1 with z_j stored normalised
-  // (z_j / gamma_j); the buffers hold w_k scaled by the a1 that made it, so
-  // that the update needs no product with z: a1 w_{j+1} = z_j - (a3/a1'') (a1'' w_{j-1})
-  // - (a2/a1') (a1' w_j), and x += (c_{j+1} eta / a1) (a1 w_{j+1})
+  const double inv = 1.0 / a1;
+  const double cn = a0 * inv, sn = gn * inv;
   st->w_a = 1.0;
-  st->w_b = -a3 / st->a1_old2;
-  st->w_c = -a2 / st->a1_old;
-  st->x_coef = cn * st->eta / a1;
-  st->a1_old2 = st->a1_old;
-  st->a1_old = a1;
+  st->w_b = wb;
+  st->w_c = wc;
+  st->x_coef = cn * st->eta * inv;
+  st->a1inv_old2 = st->a1inv_old;
+  st->a1inv_old = inv;
   st->eta = -sn * st->eta;
   st->c_old = c;
   st->c = cn;
@@ -920,10 +981,11 @@ static __global__ void __launch_bounds__(256) k_ingest(IngestArgs a0, const Inge
   st->s = st->s_old = 0.0;
   st->delta = 0.0;
   st->gam = st->gam_old = st->gam1 = 1.0;
-  st->a1_old = st->a1_old2 = 1.0;
+  st->a1inv_old = st->a1inv_old2 = 1.0;
   st->eta = st->eta_x = 0.0;
   st->rho = 0.0;
   st->iter = 0;
+  st->entries = 0;
   st->check = 0;
   st->lucky = 0;
   st->checks = 0;

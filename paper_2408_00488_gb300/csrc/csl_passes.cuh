@@ -325,30 +325,35 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
 // End of a MID pass: grid sum of the Parseval partials; the last CTA either
 // starts MINRES (scalar_mode 1: gamma_1 = sqrt(<P^{-1} r0, r0>)) or runs the
 // Givens step of the iteration (scalar_mode 2).
+// pre: the state as the kernel found it (state_prefetch), or null
 template <typename T>
-__device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, int nblk) {
+__device__ void mid_scalar_tail(const StridedArgs<T>& a, double g2acc, int bid, int nblk,
+                                const DevState* pre = nullptr) {
   double v[1] = {g2acc}, tot[1];
   if (!grid_sum_last_block<1>(v, a.partials, &a.st->tickets[TICKET_MID], tot, bid, nblk)) return;
   if (threadIdx.x != 0) return;
-  DevState* st = a.st;
+  // the scalar step runs on a register copy of the state and stores the
+  // fields it sets
+  DevState q = pre ? *pre : *a.st;
   if (a.scalar_mode == 1) {
     const double g2 = tot[0];
     // f = 0 never reaches this pass (the ingest closes the solve with z = 0),
     // so <P^{-1} r0, r0> = 0 for a positive definite P is an underflow
     if (!(g2 > 0.0) || !(g2 < 1e300)) {
-      st->done = 1;
-      st->status = ST_BREAKDOWN;
-      return;
+      q.done = 1;
+      q.status = ST_BREAKDOWN;
+    } else {
+      q.gam = sqrt(g2);
+      q.gam1 = q.gam;
+      q.gam_old = 1.0;
+      q.eta = q.gam;
+      q.eta_x = q.gam;
+      q.rho = q.r0norm / q.gam;  // exact at the start vector
     }
-    st->gam = sqrt(g2);
-    st->gam1 = st->gam;
-    st->gam_old = 1.0;
-    st->eta = st->gam;
-    st->eta_x = st->gam;
-    st->rho = st->r0norm / st->gam;  // exact at the start vector
-    return;
+  } else {
+    givens_step(&q, tot[0]);
   }
-  givens_step(st, tot[0]);
+  store_scalar_fields(a.st, q);
 }
 
 template <typename T, int N, int WIDE, bool MID>
@@ -380,6 +385,9 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   }
   pdl_wait();
   if (a.st && a.st->done) return;
+  __shared__ DevState s_pre;
+  if (MID && a.scalar_mode != 0) state_prefetch(&s_pre, a.st);
+  if (MID && a.scalar_mode == 2 && bid == 0 && threadIdx.x == 0) a.st->entries += 1;  // read by the next stencil pass
   int logC = 0;
   while ((1 << logC) < C) ++logC;
   const int myl = threadIdx.x / TPL, t = threadIdx.x - myl * TPL;
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
     }
   }
   pdl_trigger();
-  if (MID && a.scalar_mode != 0) mid_scalar_tail<T>(a, g2acc, bid, nblk);
+  if (MID && a.scalar_mode != 0) mid_scalar_tail<T>(a, g2acc, bid, nblk, &s_pre);
 }
 
 // ---------------------------------------------------------------------------
