@@ -310,7 +310,7 @@ def run_profile(name):
     s = getattr(W, name)()
     faces = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in s.faces]
     f = torch.from_numpy(np.ascontiguousarray(s.f)).cuda()
-    for prec in (("fp32", "fp64") if name == "config1" else ("bf16x6", "bf16x3", "fp32")):
+    for prec in (("fp32", "fp32_precond", "fp64") if name == "config1" else ("bf16x6", "bf16x3", "fp32")):
         with csl.Plan(faces, s.lam, precision=prec) as plan:
             plan.solve(f, tol=TOL, maxit=MAXIT)
             torch.cuda.synchronize()
@@ -373,8 +373,8 @@ def main():
                          "written after them, so that a later (e.g. profiled) run takes the same shapes")
     ap.add_argument("--profile", choices=["config1", "config2"], default=None,
                     help="solve once, then launch each kernel of one MINRES iteration inside an "
-                         "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32 "
-                         "and fp64 forms, config2: bf16x6, bf16x3 and fp32; no JSON")
+                         "NVTX range 'prof' for an ncu capture (--nvtx --nvtx-include prof/); config1: fp32, "
+                         "fp32_precond and fp64 forms, config2: bf16x6, bf16x3 and fp32; no JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -551,6 +551,10 @@ def main():
                              "iters_min": min(its), "iters_max": max(its),
                              "max_relres": max(i.relres for i in infos)}
             B.close()
+        # one synchronisation point between dependent stages: a kernel
+        # boundary of the batch's graph (PDL) against a grid barrier of one
+        # persistent cooperative kernel
+        batched["sync_cost_us"] = {k: round(v, 3) for k, v in csl.probe_sync_cost().items()}
 
     # ---- config 2 (3D n = 127): FFT vs split-BF16 tensor-core transforms ---
     cfg2 = None

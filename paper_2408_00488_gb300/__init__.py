@@ -7,6 +7,7 @@ wrapper.  PyTorch supplies device memory and streams only.
 """
 from ._binding import (Batch, BREAKDOWN, CSLError, CUDA_ERROR, INVALID_ARG, Info, NOT_CONVERGED, OK,  # noqa: F401
                        Helmholtz, OUT_OF_MEMORY, PREC_BF16X3, PREC_BF16X6, PREC_FP32, PREC_FP64, ParaDiag, Plan,
-                       SINGULAR_PRECOND, TIMEOUT, UNSUPPORTED_SIZE, lib, precondition_static, status_string,
+                       SINGULAR_PRECOND, TIMEOUT, UNSUPPORTED_SIZE, lib, precondition_static, probe_sync_cost,
+                       status_string,
                        tune_cache_load, tune_cache_save, version)
 from .autograd import CSLSolve, solve  # noqa: F401

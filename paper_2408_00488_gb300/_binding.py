@@ -67,6 +67,7 @@ _SIGS = {
     "csl_paradiag_destroy": (None, [_P]),
     "csl_test_convert_d2f": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "csl_test_convert_f2d": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "csl_probe_sync_cost": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "csl_version": (ctypes.c_char_p, []),
     "csl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "csl_last_error": (ctypes.c_char_p, []),
@@ -523,6 +524,18 @@ def test_convert(x, out_dtype, stream=None):
         raise ValueError("float64 -> float32 or float32 -> float64")
     _check(st, "csl_test_convert")
     return out
+
+
+def probe_sync_cost(kernels: int = 200, barriers: int = 1000, unreachable: bool = False):
+    """Measurement hook (include/csl_testing.h): microseconds per kernel
+    boundary of a CUDA graph of stage-shaped kernels with and without
+    programmatic dependent launch, and per grid barrier of one cooperative
+    kernel.  With unreachable=True every barrier wait runs out of its budget
+    and CSLError(TIMEOUT) is raised."""
+    out = (ctypes.c_double * 3)()
+    st = lib.csl_probe_sync_cost(int(kernels), int(barriers), 1 if unreachable else 0, out)
+    _check(st, "csl_probe_sync_cost")
+    return {"graph_pdl_us": out[0], "graph_us": out[1], "grid_barrier_us": out[2]}
 
 
 class ParaDiag:

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcsl.so")
-SOURCES = ["csl_api.cu", "csl_pass64.cu", "csl_pass32.cu", "csl_pass64_big.cu", "csl_pass32_big.cu", "csl_cluster.cu", "csl_static.cu", "csl_tc.cu", "csl_paradiag.cu", "csl_helmholtz.cu"]
+SOURCES = ["csl_api.cu", "csl_pass64.cu", "csl_pass32.cu", "csl_pass64_big.cu", "csl_pass32_big.cu", "csl_cluster.cu", "csl_static.cu", "csl_tc.cu", "csl_paradiag.cu", "csl_helmholtz.cu", "csl_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "--expt-relaxed-constexpr"]

@@ -46,6 +46,9 @@ cudaError_t launch_row_big(int N, int load, int store, const RowArgs<T>& a, cons
                            const RowArgs<T>* batch, int nsys) {
   if (N == 16384) {  // FP64 only, single systems: two-CTA cluster per line
     if constexpr (sizeof(T) == 8) {
+      // the FP64 form's vectors are FP64 in the plain modes
+      if (load == LOAD_LANCZOS_V64) load = LOAD_LANCZOS;
+      if (store == STORE_Z_UPDATE_V64) store = STORE_Z_UPDATE;
       if (!batch) return launch_row_cl(load, store, a, L, s);
     }
     return cudaErrorInvalidValue;

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const StridedArgs<float> a = batch ? batch[sys] : a0;
   pdl_wait();
   if (a.st && a.st->done) return;
+  if (MID && a.scalar_mode == 2 && bid == 0 && threadIdx.x == 0) a.st->entries += 1;  // read by the next stencil pass
 
   extern __shared__ __align__(128) unsigned char tc_smem[];
   unsigned char* sB = tc_smem;                  // SPLIT sine-matrix terms
