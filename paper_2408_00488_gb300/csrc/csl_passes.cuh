@@ -22,6 +22,15 @@
 // FP32 passes: two CTAs of 256 threads per SM (at most 128 registers per
 // thread); the FP64 lines need the full register file
 #define CSL_PASS_MINB(T, V) (sizeof(T) == 4 && (V) < 3 ? ((V) == 2 ? 3 : 2) : 1)
+// The warp-per-line row passes of length 1024 that stream MINRES vectors
+// from HBM (the Lanczos step before the forward transform, the w/x update
+// after the inverse one) keep many loads in flight per lane, so they take the
+// whole register file: one CTA per SM, which is what their grids give (a
+// 256-thread CTA of 8 lines: 128 CTAs at n = 1023).
+#define CSL_ROW_STREAMS(T, N, V, LOAD_MODE, STORE_MODE) \
+  (sizeof(T) == 4 && (N) == 1024 && (V) == 0 && ((LOAD_MODE) >= 2 || (STORE_MODE) >= 3))
+#define CSL_ROW_MINB(T, N, V, LOAD_MODE, STORE_MODE) \
+  (CSL_ROW_STREAMS(T, N, V, LOAD_MODE, STORE_MODE) ? 1 : CSL_PASS_MINB(T, V))
 
 namespace csl {
 
@@ -102,7 +111,8 @@ __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
 
 template <typename T, int N, int WIDE, int LOAD_MODE, int STORE_MODE>
-__global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, WIDE)) k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
+__global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_ROW_MINB(T, N, WIDE, LOAD_MODE, STORE_MODE))
+    k_row(RowArgs<T> a0, const RowArgs<T>* batch, int bps) {
   // the V64 modes are the Lanczos / update modes with FP64 vectors
   constexpr int LOAD = LOAD_MODE == LOAD_LANCZOS_V64 ? LOAD_LANCZOS : LOAD_MODE;
   constexpr int STORE = STORE_MODE == STORE_Z_UPDATE_V64 ? STORE_Z_UPDATE : STORE_MODE;
@@ -116,10 +126,12 @@ __global__ void __launch_bounds__(pass_max_threads<N, WIDE>(), CSL_PASS_MINB(T, 
   const RowArgs<T> a = batch ? batch[sys] : a0;
   constexpr int TPL = D::TPL, LS = D::LS;
   constexpr int NL = (N + TPL - 1) / TPL;  // elements per lane
-  // load batch: the Lanczos and update variants keep 2 and 4 16-byte vector
-  // values (FP64, or float pairs) per element in flight, so they batch fewer
-  // elements (128-register FP32 budget)
-  constexpr int UBMAX = STORE == STORE_Z_UPDATE ? 2 : LOAD == LOAD_LANCZOS ? 4 : 8;
+  // load batch (elements per lane in flight): the Lanczos variant holds two
+  // 16-byte vector values (FP64, or float pairs) per element, the update
+  // variant four; with the FP32 transform the warp-per-line form has the
+  // whole register file for them (CSL_ROW_MINB)
+  constexpr bool wide_batch = CSL_ROW_STREAMS(T, N, WIDE, LOAD_MODE, STORE_MODE);
+  constexpr int UBMAX = STORE == STORE_Z_UPDATE ? (wide_batch ? 4 : 2) : LOAD == LOAD_LANCZOS ? (wide_batch ? 16 : 4) : 8;
   constexpr int UB = NL < UBMAX ? NL : UBMAX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c_t* w_tw = (c_t*)smem_raw;
