@@ -1154,7 +1154,8 @@ csl_status csl_plan_create(csl_plan** out, int dim, const int64_t n[3], const do
   }
   {
     // one warp per strip, 8 warps per CTA
-    P->sten_strip = P->ff ? strip_rows(dim, nx, ny, nz, kSMs) : kStencilStrip;
+    P->sten_strip = P->ff ? strip_rows(dim, nx, ny, nz, kSMs, 24)
+                    : dim == 2 ? strip_rows(dim, nx, ny, nz, kSMs, 16) : kStencilStrip;
     const long blocks = (stencil_strips(dim, nx, ny, nz, P->sten_strip) + 7) / 8;
     P->sten_blocks = (int)(blocks < kSMs * 8 ? blocks : kSMs * 8);
   }

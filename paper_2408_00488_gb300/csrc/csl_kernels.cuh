@@ -226,8 +226,9 @@ __device__ __forceinline__ float2 shfl_down_f2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
-// Rows (2D) or planes (3D) one warp walks per strip of the FP64-arithmetic
-// stencil; the float-pair stencil sizes its strips per plan (strip_rows).
+// Planes one warp walks per strip of the 3D FP64-arithmetic stencil; the
+// float-pair stencil and the 2D FP64 one size their strips per plan
+// (strip_rows).
 constexpr int kStencilStrip = 16;
 
 __device__ __forceinline__ double2 shfl_up_d2(double2 v) {
@@ -245,13 +246,15 @@ __host__ __device__ inline long stencil_strips(int dim, int nx, int ny, int nz, 
   return nsx * ((nm + strip - 1) / strip) * (dim == 3 ? ny : 1);
 }
 
-// Strip length of the float-pair stencil: enough strips for 24 warps on each
-// of the 152 SMs (three 8-warp CTAs at 80 registers), so that the dependent
-// pair arithmetic of one warp hides behind the others; 4 .. 64 steps.
-inline int strip_rows(int dim, int nx, int ny, int nz, int sms) {
+// Strip length for `warps` resident warps on each of the `sms` SMs: 24 for
+// the float-pair stencil (three 8-warp CTAs at 80 registers), 16 for the 2D
+// FP64-arithmetic stencil (two at 128), so that the dependent arithmetic of
+// one warp hides behind the others and every SM gets the same number of
+// strips; 4 .. 64 steps.
+inline int strip_rows(int dim, int nx, int ny, int nz, int sms, int warps) {
   const long cols = (long)((nx + 31) / 32) * (dim == 3 ? ny : 1);
   const long nm = dim == 2 ? ny : nz;
-  long per_col = (long)sms * 24 / cols;
+  long per_col = (long)sms * warps / cols;
   if (per_col < 1) per_col = 1;
   const long strip = (nm + per_col - 1) / per_col;
   return (int)(strip < 4 ? 4 : strip > 64 ? 64 : strip);
@@ -419,7 +422,8 @@ __host__ __device__ constexpr int ff_stencil_smem(int dim) {
 // add the beta block term, delta and u' = A ẑ - lanc v_{j-1} (v held as float
 // pairs) in pairs too: no FP64 arithmetic per point.
 template <int DIM, typename TZ, bool FF, bool VP>
-__global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 1) k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
+__global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : (DIM == 2 ? 2 : 1))
+    k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
   static_assert(!FF || (sizeof(TZ) == 8 && VP), "the float-pair stencil reads an FP32 z and pair vectors");
   static_assert(!VP || sizeof(TZ) == 8, "pair vectors go with an FP32 z");
   const int sys = batch ? (int)(blockIdx.x / bps) : 0;
