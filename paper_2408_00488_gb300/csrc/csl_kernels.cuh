@@ -460,8 +460,10 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : (DIM == 2 ? 2 :
   const long mstride = DIM == 2 ? (long)nx : (long)nx * ny;
   const int lane = threadIdx.x & 31;
   const int strip = a.strip;
-  const long nsx = (nx + 31) / 32, nsm = (nm + strip - 1) / strip;
-  const long nstrips = stencil_strips(DIM, nx, ny, a.g.nz, strip);
+  // strip indices in 32 bits (a plan has far fewer than 2^32 strips): one
+  // 32-bit division per strip instead of 64-bit ones
+  const unsigned nsx = (unsigned)(nx + 31) / 32u, nsm = (unsigned)(nm + strip - 1) / (unsigned)strip;
+  const unsigned nstrips = (unsigned)stencil_strips(DIM, nx, ny, a.g.nz, strip);
   double acc[2] = {0.0, 0.0};
   ff2 dacc = {0.f, 0.f};
   float2 beta2 = make_float2(0.f, 0.f), lanc2 = make_float2(0.f, 0.f);
@@ -469,11 +471,12 @@ __global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : (DIM == 2 ? 2 :
     beta2 = d_to_ff(beta);
     lanc2 = d_to_ff(lanc);
   }
-  for (long s = (long)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
-       s += (long)nblk * (blockDim.x >> 5)) {
-    const int sx = (int)(s % nsx);
-    const int sm = (int)((s / nsx) % nsm);
-    const int yfix = DIM == 3 ? (int)(s / (nsx * nsm)) : 0;
+  for (unsigned s = (unsigned)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nstrips;
+       s += (unsigned)nblk * (blockDim.x >> 5)) {
+    const unsigned q = s / nsx;  // 2D: q < nsm; 3D: q = yfix * nsm + sm
+    const int sx = (int)(s - q * nsx);
+    const int sm = DIM == 3 ? (int)(q % nsm) : (int)q;
+    const int yfix = DIM == 3 ? (int)(q / nsm) : 0;
     const int x = sx * 32 + lane;
     const bool vx = x < nx;
     const int m0 = sm * strip, m1 = min(m0 + strip, nm);
