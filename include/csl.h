@@ -365,8 +365,8 @@ size_t csl_batch_workspace_bytes(const csl_batch* batch);
  * library, held by every GPU that loads it until the process exits and
  * shared by all calls: calls that overlap on the GPU race and must be
  * serialised by the caller.  Every call rewrites all the scratch it reads.
- * The first call on a device performs a one-time set-up (looking up the
- * arrays' device addresses) and should come before any stream capture.
+ * The first call on a device performs a one-time set-up: it looks up the
+ * arrays' device addresses (cudaGetSymbolAddress) with that device current.
  */
 csl_status csl_precondition_static(int dim, const int64_t n[3], double gamma, double alpha, double beta,
                                    int precision, const double* v, double* out, void* stream);

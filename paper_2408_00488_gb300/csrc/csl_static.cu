@@ -12,8 +12,7 @@
 // intermediate it reads, so nothing needs clearing between calls.
 //
 // Set-up: the first call on a device looks up the device addresses of the
-// arrays (cudaGetSymbolAddress) with that device current; it should come
-// before any stream capture.
+// arrays (cudaGetSymbolAddress) with that device current.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
