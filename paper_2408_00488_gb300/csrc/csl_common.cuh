@@ -178,13 +178,16 @@ __device__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned 
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) partials[bid * NV + i] = v[i];
-    __threadfence();
-    unsigned int t = atomicAdd(ticket, 1u);
+    // one acquire-release arrival: the release orders this thread's partial
+    // stores before it, and the last arrival's acquire orders every other
+    // CTA's partials before this CTA's reads below (the CTA barrier passes
+    // that order on to the other threads)
+    unsigned int t;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
     s_last = (t == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!s_last) return false;
-  __threadfence();
   double acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
