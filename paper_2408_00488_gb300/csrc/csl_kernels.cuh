@@ -422,7 +422,7 @@ __host__ __device__ constexpr int ff_stencil_smem(int dim) {
 // add the beta block term, delta and u' = A ẑ - lanc v_{j-1} (v held as float
 // pairs) in pairs too: no FP64 arithmetic per point.
 template <int DIM, typename TZ, bool FF, bool VP>
-__global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : (DIM == 2 ? 2 : 1))
+__global__ void __launch_bounds__(256, FF ? (DIM == 2 ? 3 : 2) : 2)
     k_stencil(StencilArgs a0, const StencilArgs* batch, int bps) {
   static_assert(!FF || (sizeof(TZ) == 8 && VP), "the float-pair stencil reads an FP32 z and pair vectors");
   static_assert(!VP || sizeof(TZ) == 8, "pair vectors go with an FP32 z");
